@@ -1,0 +1,339 @@
+"""Benchmark of one DBaS-Log-MPPI step (arXiv 2504.06437) on GB300.
+
+Metric: sample-timesteps per second of one MPPI iteration (K samples x T
+steps / step time) on the planar-quadrotor workload (K=4096, T=50,
+40 obstacles, 7 shape points), with p50/p99 step latency.
+
+* value: device-resident inputs, one step = one kernel launch
+  (mppi_step_device); each step timed with CUDA events on the launching
+  stream; L2 flushed (256 MB write) between steps, outside the timed events.
+* e2e: the public host API (mppi_step with host x0/xref + mppi_get_control),
+  host<->device copies inside the timed region, wall clock per step.
+* roofline: the step kernel against the FP32 issue rate of the GPU.
+* cpu_baseline: the CPU FP64 oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle alone on the same workload.
+Multi-GPU (torchrun): every rank runs its own controller (replicas only,
+weak scaling); value = all ranks' sample-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sample-timesteps/sec per MPPI step"
+UNIT = "sample-steps/s"
+OPS_PER_PAIR = 8          # 2 sub, 2 fma (h), max (floor), rcp, add, min (collision)
+OPS_PER_SAMPLE_STEP = 135  # Philox (~80), NLN map (~20), dynamics + costs (~35)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def algorithmic_ops(K, T, P, J):
+    return K * T * (OPS_PER_PAIR * P * J + OPS_PER_SAMPLE_STEP)
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2504_06437_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def traffic_per_launch(workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")))
+    except Exception:
+        return None
+    r = rec.get(workload)
+    if not r or r.get("kernel_src_sha") != kernel_src_sha():
+        return None
+    return r.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        for line in open(self.tmp.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_rate(world, n_samples, min_seconds, max_steps=None, threads=None):
+    """Time the CPU oracle's full step on the first n_samples samples of the
+    workload; returns (sample-steps/s, steps, seconds, threads)."""
+    import oracle
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    p = dict(world.params)
+    p["K"] = n_samples
+    ctl = oracle.new_controller(p)
+    x = world.x_start
+    xref = world.reference(x)
+    oracle.step(p, world.obstacles, x, xref, ctl)  # warm
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.step(p, world.obstacles, x, xref, ctl)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps and steps >= max_steps) or (not max_steps and el >= min_seconds and steps >= 3):
+            break
+    return n_samples * p["T"] * steps / el, steps, el, oracle.get_threads()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def world_for(workload, seed):
+    from paper_2504_06437_gb300 import workloads as W
+    return W.PRESETS[workload](seed)
+
+
+def describe(world):
+    p = world.params
+    P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
+    return {"workload": world.name, "K": int(p["K"]), "T": int(p["T"]),
+            "obstacles": int(world.obstacles.shape[0]), "shape_points": P,
+            "model": "planar quadrotor" if p["model"] == 1 else "unicycle",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    world = world_for(args.workload, 0)
+    p = world.params
+    n_samples = min(int(p["K"]), args.ref_samples)
+    threads = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    pp = dict(p)
+    pp["K"] = n_samples
+    ctl = oracle.new_controller(pp)
+    x = world.x_start
+    xref = world.reference(x)
+    for _ in range(args.warmup):
+        oracle.step(pp, world.obstacles, x, xref, ctl)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.step(pp, world.obstacles, x, xref, ctl)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n_samples * pp["T"] / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": describe(world),
+            "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)),
+                           "p99": 1e3 * float(np.percentile(times, 99))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle",
+                             "sample": f"full oracle step on {n_samples} of {p['K']} samples, "
+                                       f"{args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="quad2d")
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-samples", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    from paper_2504_06437_gb300 import binding
+
+    torch.cuda.set_device(local)
+    binding.load()
+    world = world_for(args.workload, rank)
+    p = world.params
+    K, T, n = int(p["K"]), int(p["T"]), world.n
+    P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
+    J = int(world.obstacles.shape[0])
+    ctl = binding.Controller(p)
+    ctl.set_obstacles(world.obstacles)
+    x0 = world.x_start
+    xref = world.reference(x0)
+    d_in = torch.tensor(np.concatenate([x0, xref.ravel()]), dtype=torch.float64, device="cuda")
+    d_x0 = d_in.data_ptr()
+    d_xref = d_x0 + 8 * n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        ctl.step_device(d_x0, d_xref, stream)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.2)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i & 7))
+        starts[i].record(stream)
+        ctl.step_device(d_x0, d_xref, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    times_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    ms_local = float(times_ms.mean())
+    ms = allmax(ws, ms_local)
+    value = ws * K * T / (ms / 1e3)
+
+    # end to end through the host API (pinned staging inside the library)
+    u0 = ctl.get_control()
+    e2e_t = []
+    for i in range(args.e2e_steps):
+        flush.fill_(float(i & 7))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctl.step(x0, xref, stream)
+        u0 = ctl.get_control()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = allmax(ws, 1e3 * float(np.mean(e2e_t)))
+    h2d, d2h = ctl.io_bytes()
+    tiling = ctl.tiling()
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_tops = sms * 128 * f_max / 1e12
+    achieved_tops = algorithmic_ops(K, T, P, J) / (ms_local / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TOP/s",
+                "frac": achieved_tops / peak_tops, "traffic": traffic_per_launch(world.name),
+                "kernel": "step_kernel", "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz",
+                "ops_per_launch": algorithmic_ops(K, T, P, J)}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved_tops / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(describe(world), parallelism=f"replicas x{ws}", tiling=tiling),
+            "latency_ms": {"p50": float(np.percentile(times_ms, 50)),
+                           "p99": float(np.percentile(times_ms, 99))},
+            "e2e": {"value": ws * K * T / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "latency_ms": {"p50": 1e3 * float(np.percentile(e2e_t, 50)),
+                                   "p99": 1e3 * float(np.percentile(e2e_t, 99))}},
+            "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline}
+    if not args.no_cpu_baseline and ws == 1:
+        threads = os.cpu_count() or 1
+        rate, steps, el, used = oracle_rate(world, min(K, args.ref_samples), args.cpu_seconds,
+                                            threads=threads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": f"full oracle step on {min(K, args.ref_samples)} of {K} "
+                                          f"samples (T={T}, J={J}, P={P}), {steps} steps in {el:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * dbasmppi.h -- C ABI of the GB300 (sm_103a) DBaS-Log-MPPI step.
+ *
+ * One call of mppi_step() runs one outer-loop body of Algorithm 1 of
+ * "Safe Navigation ... DBaS-Log-MPPI" (arXiv 2504.06437) on the GPU for one
+ * controller: K perturbed control sequences drawn from the normal-log-normal
+ * mixture (Eq. 11) scaled by the exploration rate S_e, rolled out through
+ * the dynamics f (Eq. 1, 8) with the discrete barrier state (Eq. 5-7), scored
+ * with the DBaS cost-to-go (Eq. 9), combined by min-shifted exponentiated
+ * weights (Eq. 4), then the nominal rollout of U* gives C_B and the next S_e
+ * (Eq. 10), and the sequence is shifted for the next call.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (MPPI_OK) on success, a negative MPPI_E* code on failure;
+ *     mppi_last_error() then describes the failure (thread-local text).
+ *   - The library copies every array it is given; the caller keeps
+ *     ownership of its buffers.  A context is owned by the library from
+ *     mppi_create() until mppi_destroy(); mppi_destroy(NULL) is a no-op.
+ *   - A context is used from one host thread at a time.
+ *   - "stream" is a cudaStream_t passed as void*; NULL selects the
+ *     context's own stream.  mppi_step*() only enqueue work; the mppi_get_*()
+ *     calls synchronise with the stream of the last step.
+ *   - Device work that times out on a bounded wait reports MPPI_ETIMEOUT at
+ *     the next mppi_get_*() call.
+ */
+#ifndef DBASMPPI_H
+#define DBASMPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define MPPI_OK 0
+#define MPPI_EINVAL (-1)   /* bad argument: shape, NaN, range */
+#define MPPI_ENOMEM (-2)   /* device or pinned allocation failed / admission */
+#define MPPI_ECUDA (-3)    /* a CUDA runtime call failed */
+#define MPPI_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define MPPI_ESTATE (-5)   /* call out of order (e.g. no step yet) */
+
+/* Dynamics (Eq. 1).  MPPI_UNICYCLE: state (x, y, theta), control (v, omega),
+ * x' = x + v cos(theta) dt, y' = y + v sin(theta) dt, theta' = theta + omega dt.
+ * MPPI_QUAD2D: planar quadrotor with the constants of Sec. IV-A, state
+ * (y, z, phi, ydot, zdot, phidot), control (u1, u2) = thrust deviations with
+ * F_i = m g / 2 + u_i; explicit Euler with the right-hand side at step k as
+ * in Eq. 12. */
+#define MPPI_UNICYCLE 0
+#define MPPI_QUAD2D 1
+
+/* Size limits. */
+#define MPPI_MAX_T 256        /* horizon */
+#define MPPI_MAX_K (1 << 22)  /* samples */
+#define MPPI_MAX_OBSTACLES 4096
+#define MPPI_MAX_SHAPE 8      /* shape points per body */
+
+/* Problem parameters.  Names follow the paper: K = M samples, T = N horizon,
+ * dt (Sec. IV), lambda the temperature of Eq. 4 (the cost is divided by it),
+ * Sigma_u the 2x2 sampling covariance, (ln_mu, ln_sigma) the log-normal factor
+ * of Eq. 11, mu_coarse the coarseness factor mu of Eq. 10 (<= 0 keeps
+ * S_e = 1), gamma_ctrl the control-cost gamma of Eq. 9, gamma_bas the gamma
+ * in (0,1) of Eq. 7, R_B the barrier-state weight of Eq. 9.  The barrier is
+ * B(h) = 1 / max(h, h_eps) with h = |p_i - c_j|^2 - r_j^2 over all shape
+ * points i and obstacles j (Eq. 13/15), fused by summation; a step with some
+ * h <= 0 is a collision and adds C_coll to the cost.  Q, Qf are the diagonal
+ * stage and terminal weights over the n state entries; the control box
+ * [u_min, u_max] is G(u) <= 0 of Eq. 2 and is applied by clamping.  x_goal is
+ * x_d of Eq. 7.  shape holds n_shape body-frame points (sx, sy), placed at
+ * position + R(heading) (sx, sy).  seed keys the Philox4x32-10 generator.
+ * mass, inertia, arm, gravity are the quadrotor constants (unused by the
+ * unicycle). */
+typedef struct mppi_params {
+  int32_t model;
+  int32_t K, T;
+  double dt, lambda;
+  double sigma[4];
+  double ln_mu, ln_sigma;
+  double mu_coarse;
+  double gamma_ctrl, gamma_bas;
+  double R_B, C_coll, h_eps;
+  double Q[6], Qf[6];
+  double u_min[2], u_max[2];
+  double x_goal[6];
+  int32_t n_shape;
+  double shape[2 * MPPI_MAX_SHAPE];
+  uint64_t seed;
+  double mass, inertia, arm, gravity;
+} mppi_params;
+
+/* Kernel launch shape.  Zero fields are chosen by the library. */
+typedef struct mppi_tiling {
+  int32_t samples_per_cta;  /* S, 1..32 */
+  int32_t threads;          /* 64, 128, 256 or 512 */
+  int32_t positions_per_thread; /* 4, 8 or 16 */
+  int32_t chunk_steps;      /* time steps per chunk */
+} mppi_tiling;
+
+typedef struct mppi_ctx mppi_ctx;
+
+/* Create a controller.  u_init: T x 2 initial control sequence (row t =
+ * u_t), or NULL for zeros.  S_e starts at mu ln(e) = mu (Eq. 10 with
+ * C_B = 0).  Errors: MPPI_EINVAL (sizes beyond the limits, Sigma_u not
+ * symmetric positive semi-definite, Sigma_u singular while gamma_ctrl != 0,
+ * lambda <= 0, gamma_bas outside (0,1), h_eps <= 0, u_min > u_max, non-finite
+ * values), MPPI_ENOMEM, MPPI_ECUDA. */
+int mppi_create(const mppi_params* p, const double* u_init, mppi_ctx** out);
+
+/* Same, with an explicit launch shape (NULL = automatic). */
+int mppi_create_tiled(const mppi_params* p, const double* u_init,
+                      const mppi_tiling* tiling, mppi_ctx** out);
+
+/* Replace the obstacle set.  cxcyr: J x 3 (centre x, centre y, radius) in
+ * the world frame; copied.  J may be 0 (empty set, barrier sum 0).  Errors:
+ * MPPI_EINVAL (J < 0, J > MPPI_MAX_OBSTACLES, non-finite value, radius < 0).
+ * Synchronises with the context's last stream before replacing the set. */
+int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J);
+
+/* One iteration from host data.  x0: measured state (n doubles).  xref:
+ * (T+1) x n reference, row t compared with x_t (row 0 unused), or NULL for
+ * x_goal repeated.  Copies the inputs to the device on the stream and
+ * enqueues the step; returns without waiting. */
+int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream);
+
+/* One iteration from device data (x0, xref in device memory, same layout;
+ * xref must not be NULL).  Enqueues only the step kernel. */
+int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref,
+                     void* stream);
+
+/* After a step: u0 = u*_0 (2 doubles, the control to apply) and, if U is
+ * not NULL, the shifted nominal sequence for the next step (T x 2).
+ * Synchronises. */
+int mppi_get_control(mppi_ctx* c, double* u0, double* U);
+
+/* Diagnostics of the last step (any pointer may be NULL):
+ * costs[K] (cost-to-go of Eq. 9 per sample), collided[K] (1 if any step of
+ * the sample collided), weights[K] (Eq. 4), Ustar[T x 2] (U* before the
+ * shift), scalars[8] = {rho, Z, CB_star, S_e_next, beta_used, beta_d,
+ * S_e_used, iteration}.  Synchronises. */
+int mppi_get_debug(mppi_ctx* c, double* costs, uint8_t* collided,
+                   double* weights, double* Ustar, double* scalars);
+
+/* Bytes one mppi_step() copies host -> device (x0 and xref) and one
+ * mppi_get_control(c, u0, NULL) copies device -> host. */
+int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h);
+
+/* The launch shape in use and the number of CTAs of one step. */
+int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas);
+
+/* Checkpoint / resume of the per-controller state: U (T x 2), S_e, beta,
+ * first-call flag, iteration counter.  Restoring a state reproduces the
+ * following steps exactly, since the generator is counter-based. */
+int mppi_get_state(mppi_ctx* c, double* U, double* S_e, double* beta,
+                   int32_t* first, uint64_t* iter);
+int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta,
+                   int32_t first, uint64_t iter);
+
+/* Diagnostic: the device generator's draws for iteration `iter`, samples
+ * k < K and steps t < T, without a context.  raw (K x T x 4, may be NULL)
+ * receives the Philox4x32-10 words of counter (k, t, iter_lo, iter_hi) under
+ * key (seed_lo, seed_hi); du (K x T x 2, may be NULL) the NLN perturbations
+ * of Eq. 11 for exploration rate S_e, before clamping.  Allocates its own
+ * device scratch; synchronises.  Errors: MPPI_EINVAL (K*T > 2^26, S_e <= 0,
+ * bad params), MPPI_ENOMEM, MPPI_ECUDA. */
+int mppi_debug_draws(const mppi_params* p, double S_e, uint64_t iter, int32_t K,
+                     int32_t T, uint32_t* raw, float* du);
+
+/* Release everything owned by the context.  NULL is a no-op. */
+int mppi_destroy(mppi_ctx* c);
+
+/* Text of the last error on this host thread ("" if none). */
+const char* mppi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBASMPPI_H */

@@ -105,6 +105,10 @@ def _load():
         lib.orc_step.argtypes = [C.POINTER(_Params), dp, C.c_int32, dp, dp,
                                  C.POINTER(_State), C.POINTER(_Out)]
         lib.orc_step.restype = C.c_int
+        lib.orc_sample_costs.argtypes = [C.POINTER(_Params), dp, C.c_int32, dp, dp,
+                                         C.POINTER(_State), C.POINTER(C.c_int32), C.c_int32,
+                                         dp, C.POINTER(C.c_uint8), dp]
+        lib.orc_sample_costs.restype = C.c_int
         lib.orc_set_threads.argtypes = [C.c_int]
         lib.orc_get_threads.restype = C.c_int
         _lib = lib
@@ -300,3 +304,24 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
     res["U_next"] = U.copy()
     res["S_e_next"] = ctl.S_e
     return res
+
+
+def sample_costs(cfg: dict, obstacles, x0, xref, ctl: Controller, ks) -> dict:
+    """Cost-to-go, collision flag and min h of the listed samples, from the
+    state ``ctl`` (not modified)."""
+    lib = _load()
+    p = make_params(cfg)
+    T, n = p.T, state_dim(p.model)
+    ob = np.ascontiguousarray(_f64(obstacles).reshape(-1, 3))
+    x0 = _f64(x0)
+    xref = _f64(xref, (T + 1, n))
+    U = np.ascontiguousarray(ctl.U, dtype=np.float64).reshape(T, 2).copy()
+    st = _State(U=_dp(U), S_e=ctl.S_e, beta=ctl.beta, first=int(ctl.first), iter=ctl.iter)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    S = np.zeros(ks.size)
+    coll = np.zeros(ks.size, dtype=np.uint8)
+    mh = np.zeros(ks.size)
+    lib.orc_sample_costs(C.byref(p), _dp(ob), ob.shape[0], _dp(x0), _dp(xref), C.byref(st),
+                         ks.ctypes.data_as(C.POINTER(C.c_int32)), ks.size, _dp(S),
+                         coll.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(mh))
+    return dict(costs=S, coll=coll, minh=mh)

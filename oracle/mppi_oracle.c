@@ -460,3 +460,31 @@ void orc_noise_batch(const orc_params* p, double S_e, int32_t K, int32_t T,
       orc_noise(p, S_e, k, t, iter, du + ((size_t)k * T + t) * 2,
                 z ? z + ((size_t)k * T + t) * 4 : NULL);
 }
+
+/* Cost-to-go (Eq. 9) of selected samples only, for comparisons at sizes where
+ * the full step is too slow: the state (U, S_e, beta, first, iter) is the one
+ * the step would start from.  ks[i] are sample indices; outputs per index. */
+int orc_sample_costs(const orc_params* p, const double* obst, int32_t J,
+                     const double* x0, const double* xref, const orc_state* st,
+                     const int32_t* ks, int32_t nk, double* S, uint8_t* coll,
+                     double* minh) {
+  double beta_d, B0;
+  orc_bsum(p, obst, J, p->x_goal, &beta_d, NULL, NULL);
+  orc_bsum(p, obst, J, x0, &B0, NULL, NULL);
+  double beta = st->first ? B0 : B0 - p->gamma_bas * (beta_d - st->beta);
+  double Minv[4] = {0, 0, 0, 0};
+  if (p->gamma_ctrl != 0.0) {
+    double a = st->S_e * p->sigma[0], b = st->S_e * p->sigma[1];
+    double c = st->S_e * p->sigma[2], d = st->S_e * p->sigma[3];
+    double det = a * d - b * c;
+    Minv[0] = d / det; Minv[1] = -b / det;
+    Minv[2] = -c / det; Minv[3] = a / det;
+  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_get_threads())
+#endif
+  for (int i = 0; i < nk; ++i)
+    rollout_sample(p, obst, J, x0, xref, st->U, st->S_e, beta, beta_d, st->iter,
+                   ks[i], Minv, &S[i], &coll[i], &minh[i], NULL);
+  return 0;
+}

@@ -1,0 +1,260 @@
+"""Thin ctypes binding over ``libdbasmppi.so`` (C ABI in ``include/dbasmppi.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no fallback; if the library is missing the import of
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_LIB = os.path.join(_HERE, "libdbasmppi.so")
+_SOURCES = ["csrc/dbasmppi.cu"]
+_DEPS = ["csrc/dbasmppi.cu", "csrc/mppi_device.cuh", "csrc/mppi_tile.cuh"]
+HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
+
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-shared", "-Xcompiler", "-fPIC"]
+
+MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE = 0, -1, -2, -3, -4, -5
+UNICYCLE, QUAD2D = 0, 1
+MAX_SHAPE = 8
+
+
+class MppiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _stale() -> bool:
+    if not os.path.exists(_LIB):
+        return True
+    t = os.path.getmtime(_LIB)
+    deps = [os.path.join(_HERE, d) for d in _DEPS] + [HEADER]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library in-tree for sm_103a (nvcc cross-compiles
+    without a GPU)."""
+    if not force and not _stale():
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["nvcc", *NVCC_FLAGS, "-o", tmp, *[os.path.join(_HERE, s) for s in _SOURCES]]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("model", C.c_int32), ("K", C.c_int32), ("T", C.c_int32),
+        ("dt", C.c_double), ("lam", C.c_double),
+        ("sigma", C.c_double * 4),
+        ("ln_mu", C.c_double), ("ln_sigma", C.c_double),
+        ("mu_coarse", C.c_double),
+        ("gamma_ctrl", C.c_double), ("gamma_bas", C.c_double),
+        ("R_B", C.c_double), ("C_coll", C.c_double), ("h_eps", C.c_double),
+        ("Q", C.c_double * 6), ("Qf", C.c_double * 6),
+        ("u_min", C.c_double * 2), ("u_max", C.c_double * 2),
+        ("x_goal", C.c_double * 6),
+        ("n_shape", C.c_int32),
+        ("shape", C.c_double * (2 * MAX_SHAPE)),
+        ("seed", C.c_uint64),
+        ("mass", C.c_double), ("inertia", C.c_double),
+        ("arm", C.c_double), ("gravity", C.c_double),
+    ]
+
+
+class Tiling(C.Structure):
+    _fields_ = [("samples_per_cta", C.c_int32), ("threads", C.c_int32),
+                ("positions_per_thread", C.c_int32), ("chunk_steps", C.c_int32)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def load():
+    """Load (building if needed) the library and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if _stale():
+        build()
+    lib = C.CDLL(_LIB)
+    vp = C.c_void_p
+    lib.mppi_create.argtypes = [C.POINTER(Params), _dp, C.POINTER(vp)]
+    lib.mppi_create_tiled.argtypes = [C.POINTER(Params), _dp, C.POINTER(Tiling), C.POINTER(vp)]
+    lib.mppi_set_obstacles.argtypes = [vp, _dp, C.c_int32]
+    lib.mppi_step.argtypes = [vp, _dp, _dp, vp]
+    lib.mppi_step_device.argtypes = [vp, vp, vp, vp]
+    lib.mppi_get_control.argtypes = [vp, _dp, _dp]
+    lib.mppi_get_debug.argtypes = [vp, _dp, C.POINTER(C.c_uint8), _dp, _dp, _dp]
+    lib.mppi_io_bytes.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    lib.mppi_get_tiling.argtypes = [vp, C.POINTER(Tiling), C.POINTER(C.c_int32)]
+    lib.mppi_get_state.argtypes = [vp, _dp, _dp, _dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
+    lib.mppi_set_state.argtypes = [vp, _dp, C.c_double, C.c_double, C.c_int32, C.c_uint64]
+    lib.mppi_destroy.argtypes = [vp]
+    lib.mppi_debug_draws.argtypes = [C.POINTER(Params), C.c_double, C.c_uint64, C.c_int32,
+                                     C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
+    lib.mppi_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != MPPI_OK:
+        raise MppiError(rc, load().mppi_last_error().decode())
+
+
+def make_params(cfg: dict) -> Params:
+    p = Params()
+    for name, ctype in Params._fields_:
+        key = "lambda" if name == "lam" else name
+        if key not in cfg:
+            continue
+        val = cfg[key]
+        if hasattr(ctype, "_length_"):
+            arr = np.zeros(ctype._length_)
+            v = np.asarray(val, dtype=np.float64).ravel()
+            arr[: v.size] = v
+            setattr(p, name, ctype(*arr))
+        else:
+            setattr(p, name, val)
+    if "shape" in cfg:
+        p.n_shape = int(np.asarray(cfg["shape"]).reshape(-1, 2).shape[0])
+    return p
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def debug_draws(cfg: dict, S_e: float, it: int, K: int, T: int):
+    """Device generator output: (raw words [K,T,4] uint32, du [K,T,2] float32)."""
+    p = make_params(cfg)
+    raw = np.zeros((K, T, 4), dtype=np.uint32)
+    du = np.zeros((K, T, 2), dtype=np.float32)
+    _check(load().mppi_debug_draws(C.byref(p), float(S_e), int(it), int(K), int(T),
+                                   raw.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                   du.ctypes.data_as(C.POINTER(C.c_float))))
+    return raw, du
+
+
+class Controller:
+    """One DBaS-Log-MPPI controller living on the GPU."""
+
+    def __init__(self, cfg: dict, u_init=None, tiling: dict | None = None):
+        lib = load()
+        self.cfg = dict(cfg)
+        self.params = make_params(cfg)
+        self.K, self.T = int(self.params.K), int(self.params.T)
+        self.n = 6 if self.params.model == QUAD2D else 3
+        h = C.c_void_p()
+        u = None if u_init is None else _f64(u_init).reshape(self.T, 2)
+        self._u_init = u
+        if tiling:
+            t = Tiling(**{k: int(v) for k, v in tiling.items()})
+            rc = lib.mppi_create_tiled(C.byref(self.params), _ptr(u) if u is not None else None,
+                                       C.byref(t), C.byref(h))
+        else:
+            rc = lib.mppi_create(C.byref(self.params), _ptr(u) if u is not None else None, C.byref(h))
+        _check(rc)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().mppi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_obstacles(self, obstacles):
+        ob = _f64(obstacles).reshape(-1, 3)
+        _check(load().mppi_set_obstacles(self.h, _ptr(ob) if ob.size else None, ob.shape[0]))
+
+    def step(self, x0, xref=None, stream=None):
+        x0 = _f64(x0)
+        xr = None if xref is None else _f64(xref).reshape(self.T + 1, self.n)
+        _check(load().mppi_step(self.h, _ptr(x0), _ptr(xr) if xr is not None else None,
+                                _stream_ptr(stream)))
+
+    def step_device(self, d_x0: int, d_xref: int, stream=None):
+        _check(load().mppi_step_device(self.h, C.c_void_p(d_x0), C.c_void_p(d_xref),
+                                       _stream_ptr(stream)))
+
+    def get_control(self, want_U: bool = False):
+        u0 = np.zeros(2)
+        U = np.zeros((self.T, 2)) if want_U else None
+        _check(load().mppi_get_control(self.h, _ptr(u0), _ptr(U) if want_U else None))
+        return (u0, U) if want_U else u0
+
+    def get_debug(self) -> dict:
+        K, T = self.K, self.T
+        costs = np.zeros(K)
+        coll = np.zeros(K, dtype=np.uint8)
+        w = np.zeros(K)
+        Us = np.zeros((T, 2))
+        sc = np.zeros(8)
+        _check(load().mppi_get_debug(self.h, _ptr(costs), coll.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                     _ptr(w), _ptr(Us), _ptr(sc)))
+        return dict(costs=costs, coll=coll, weights=w, Ustar=Us, rho=sc[0], Z=sc[1],
+                    CB_star=sc[2], S_e_next=sc[3], beta_used=sc[4], beta_d=sc[5],
+                    S_e_used=sc[6], iter=int(sc[7]))
+
+    def tiling(self):
+        t = Tiling()
+        n = C.c_int32()
+        _check(load().mppi_get_tiling(self.h, C.byref(t), C.byref(n)))
+        return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
+                    positions_per_thread=t.positions_per_thread, chunk_steps=t.chunk_steps,
+                    n_ctas=n.value)
+
+    def io_bytes(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        _check(load().mppi_io_bytes(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def get_state(self) -> dict:
+        U = np.zeros((self.T, 2))
+        S_e, beta = C.c_double(), C.c_double()
+        first, it = C.c_int32(), C.c_uint64()
+        _check(load().mppi_get_state(self.h, _ptr(U), C.byref(S_e), C.byref(beta), C.byref(first),
+                                     C.byref(it)))
+        return dict(U=U, S_e=S_e.value, beta=beta.value, first=bool(first.value), iter=it.value)
+
+    def set_state(self, U, S_e, beta, first, it):
+        U = _f64(U).reshape(self.T, 2)
+        _check(load().mppi_set_state(self.h, _ptr(U), float(S_e), float(beta), int(bool(first)), int(it)))

@@ -1,0 +1,632 @@
+// C ABI of the DBaS-Log-MPPI step (declared in include/dbasmppi.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/dbasmppi.h"
+#include "mppi_tile.cuh"
+
+using namespace dbm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(MPPI_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+// ------------------------------------------------------------------ kernels
+
+template <int MODEL, int NPOS>
+__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ CtrlDesc D,
+                                                   const double* __restrict__ x0,
+                                                   const double* __restrict__ xref) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ TileScratch ts;
+  if (threadIdx.x == 0) {
+    mbar_init(&ts.mbar);
+    ts.mbar_phase = 0u;
+  }
+  __syncthreads();
+  run_tile<MODEL, NPOS>(D, blockIdx.x, x0, xref, smem, ts);
+}
+
+__global__ void prep_kernel(const __grid_constant__ CtrlDesc D) {
+  __shared__ double red[64];
+  prep_constants(D, red, threadIdx.x, blockDim.x);
+}
+
+__global__ void weights_kernel(const double* __restrict__ costs, int K,
+                               const DevState* __restrict__ st, double inv_lambda,
+                               double* __restrict__ w) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) w[k] = exp(-(costs[k] - st->rho) * inv_lambda) / st->Z;
+}
+
+// Raw Philox words and NLN draws of the device generator for k < K, t < T.
+__global__ void draws_kernel(int K, int T, uint32_t k0, uint32_t k1, uint32_t it_lo, uint32_t it_hi,
+                             float L00, float L10, float L11, float ln_mu, float ln_sigma,
+                             uint32_t* __restrict__ raw, float* __restrict__ du) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K * T) return;
+  int k = i / T, t = i - k * T;
+  uint4 r = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)t, it_lo, it_hi), k0, k1);
+  if (raw) reinterpret_cast<uint4*>(raw)[i] = r;
+  if (du) reinterpret_cast<float2*>(du)[i] = nln_draw(r, L00, L10, L11, ln_mu, ln_sigma);
+}
+
+using StepFn = void (*)(CtrlDesc, const double*, const double*);
+
+StepFn pick_kernel(int model, int npos) {
+  if (model == MPPI_UNICYCLE) {
+    if (npos == 4) return step_kernel<0, 4>;
+    if (npos == 16) return step_kernel<0, 16>;
+    return step_kernel<0, 8>;
+  }
+  if (npos == 4) return step_kernel<1, 4>;
+  if (npos == 16) return step_kernel<1, 16>;
+  return step_kernel<1, 8>;
+}
+
+int state_dim(int model) { return model == MPPI_QUAD2D ? 6 : 3; }
+
+bool finite_all(const double* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+int validate(const mppi_params* p) {
+  if (!p) return fail(MPPI_EINVAL, "params is NULL");
+  if (p->model != MPPI_UNICYCLE && p->model != MPPI_QUAD2D)
+    return fail(MPPI_EINVAL, "unknown model %d", p->model);
+  if (p->K < 1 || p->K > MPPI_MAX_K) return fail(MPPI_EINVAL, "K=%d out of [1, %d]", p->K, MPPI_MAX_K);
+  if (p->T < 1 || p->T > MPPI_MAX_T) return fail(MPPI_EINVAL, "T=%d out of [1, %d]", p->T, MPPI_MAX_T);
+  if (p->n_shape < 1 || p->n_shape > MPPI_MAX_SHAPE)
+    return fail(MPPI_EINVAL, "n_shape=%d out of [1, %d]", p->n_shape, MPPI_MAX_SHAPE);
+  const double sc[] = {p->dt,      p->lambda,     p->ln_mu, p->ln_sigma, p->mu_coarse,
+                       p->gamma_ctrl, p->gamma_bas, p->R_B,   p->C_coll,   p->h_eps,
+                       p->mass,    p->inertia,    p->arm,   p->gravity};
+  if (!finite_all(sc, 14) || !finite_all(p->sigma, 4) || !finite_all(p->Q, 6) ||
+      !finite_all(p->Qf, 6) || !finite_all(p->u_min, 2) || !finite_all(p->u_max, 2) ||
+      !finite_all(p->x_goal, 6) || !finite_all(p->shape, 2 * p->n_shape))
+    return fail(MPPI_EINVAL, "non-finite parameter");
+  if (!(p->dt > 0)) return fail(MPPI_EINVAL, "dt must be > 0");
+  if (!(p->lambda > 0)) return fail(MPPI_EINVAL, "lambda must be > 0");
+  if (!(p->gamma_bas > 0 && p->gamma_bas < 1)) return fail(MPPI_EINVAL, "gamma_bas must be in (0,1)");
+  if (!(p->h_eps > 0)) return fail(MPPI_EINVAL, "h_eps must be > 0");
+  if (p->ln_sigma < 0) return fail(MPPI_EINVAL, "ln_sigma must be >= 0");
+  for (int d = 0; d < 2; ++d)
+    if (p->u_min[d] > p->u_max[d]) return fail(MPPI_EINVAL, "u_min > u_max");
+  const double* S = p->sigma;
+  if (S[1] != S[2]) return fail(MPPI_EINVAL, "Sigma must be symmetric");
+  double det = S[0] * S[3] - S[1] * S[2];
+  if (S[0] < 0 || S[3] < 0 || det < 0) return fail(MPPI_EINVAL, "Sigma must be positive semi-definite");
+  if (p->gamma_ctrl != 0 && !(S[0] > 0 && det > 0))
+    return fail(MPPI_EINVAL, "Sigma must be positive definite when gamma_ctrl != 0");
+  if (p->model == MPPI_QUAD2D && !(p->mass > 0 && p->inertia > 0))
+    return fail(MPPI_EINVAL, "quadrotor mass and inertia must be > 0");
+  return MPPI_OK;
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v > 0 ? v : 48 * 1024;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+
+struct mppi_ctx {
+  mppi_params p;
+  mppi_tiling tl;
+  int n = 3;
+  int Jcap = 0;
+  int smem = 0;
+  CtrlDesc D;
+  StepFn fn = nullptr;
+  double* d_U = nullptr;
+  float2* d_cU = nullptr;
+  float2* d_cA = nullptr;
+  DevState* d_st = nullptr;
+  double* d_obst = nullptr;
+  double* d_in = nullptr;  // x0 (n) then xref ((T+1) n)
+  float* d_part = nullptr;
+  double2* d_part_rz = nullptr;
+  float* d_gpart = nullptr;
+  double2* d_gpart_rz = nullptr;
+  unsigned* d_cnt = nullptr;
+  double* d_costs = nullptr;
+  uint8_t* d_coll = nullptr;
+  double* d_Ustar = nullptr;
+  double* d_w = nullptr;
+  double* h_in = nullptr;   // pinned staging of the inputs
+  DevState* h_st = nullptr; // pinned readback
+  double* h_U = nullptr;    // pinned readback
+  cudaStream_t own = nullptr;
+  cudaStream_t last = nullptr;
+  cudaEvent_t in_ev = nullptr;
+  bool in_ev_pending = false;
+  bool stepped = false;
+};
+
+namespace {
+
+void free_ctx(mppi_ctx* c) {
+  if (!c) return;
+  if (c->last) cudaStreamSynchronize(c->last);
+  cudaFree(c->d_U);
+  cudaFree(c->d_cU);
+  cudaFree(c->d_cA);
+  cudaFree(c->d_st);
+  cudaFree(c->d_obst);
+  cudaFree(c->d_in);
+  cudaFree(c->d_part);
+  cudaFree(c->d_part_rz);
+  cudaFree(c->d_gpart);
+  cudaFree(c->d_gpart_rz);
+  cudaFree(c->d_cnt);
+  cudaFree(c->d_costs);
+  cudaFree(c->d_coll);
+  cudaFree(c->d_Ustar);
+  cudaFree(c->d_w);
+  cudaFreeHost(c->h_in);
+  cudaFreeHost(c->h_st);
+  cudaFreeHost(c->h_U);
+  if (c->in_ev) cudaEventDestroy(c->in_ev);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+// Launch shape: S samples per CTA, chosen so the grid covers the SMs at
+// least twice when K allows; TC steps per chunk so one chunk holds about
+// threads x NPOS barrier positions; shrink until shared memory fits.
+int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tiling* out,
+                  int* smem_out) {
+  const int sms = num_sms();
+  const int n = state_dim(p->model);
+  mppi_tiling t = {0, 0, 0, 0};
+  if (req) t = *req;
+  if (t.samples_per_cta <= 0) {
+    long want = ((long)p->K + 2L * sms - 1) / (2L * sms);
+    t.samples_per_cta = (int)(want < 1 ? 1 : (want > 32 ? 32 : want));
+  }
+  if (t.samples_per_cta > 32) return fail(MPPI_EINVAL, "samples_per_cta must be <= 32");
+  if (t.threads <= 0) t.threads = 256;
+  if (t.threads != 64 && t.threads != 128 && t.threads != 256 && t.threads != 512)
+    return fail(MPPI_EINVAL, "threads must be 64, 128, 256 or 512");
+  if (t.positions_per_thread <= 0) t.positions_per_thread = 8;
+  if (t.positions_per_thread != 4 && t.positions_per_thread != 8 && t.positions_per_thread != 16)
+    return fail(MPPI_EINVAL, "positions_per_thread must be 4, 8 or 16");
+  const int SP = t.samples_per_cta * p->n_shape;
+  if (t.chunk_steps <= 0) {
+    int tc = (t.threads * t.positions_per_thread + SP - 1) / SP;
+    t.chunk_steps = tc < 1 ? 1 : tc;
+  }
+  if (t.chunk_steps > p->T) t.chunk_steps = p->T;
+  const int limit = max_smem_optin();
+  const int nTiles = (p->K + t.samples_per_cta - 1) / t.samples_per_cta;
+  int GT = (nTiles + 63) / 64;
+  if (GT < 32) GT = 32;
+  const int nGroups = (nTiles + GT - 1) / GT;
+  const int nscl = GT > nGroups ? GT : nGroups;
+  for (;;) {
+    SmemLayout L = smem_layout(p->T, t.samples_per_cta, t.chunk_steps, p->n_shape, J, n, nscl);
+    if (L.total <= limit) {
+      *smem_out = L.total;
+      break;
+    }
+    if (t.chunk_steps > 1) {
+      t.chunk_steps = (t.chunk_steps + 1) / 2;
+    } else {
+      return fail(MPPI_EINVAL, "problem needs %d bytes of shared memory (limit %d)", L.total, limit);
+    }
+  }
+  *out = t;
+  return MPPI_OK;
+}
+
+// Fill the descriptor from the parameters and the device buffers.
+void fill_desc(mppi_ctx* c) {
+  const mppi_params* p = &c->p;
+  CtrlDesc& D = c->D;
+  memset(&D, 0, sizeof(D));
+  D.model = p->model;
+  D.K = p->K;
+  D.T = p->T;
+  D.J = 0;
+  D.P = p->n_shape;
+  D.n = c->n;
+  D.S = c->tl.samples_per_cta;
+  D.TC = c->tl.chunk_steps;
+  D.NPOS = c->tl.positions_per_thread;
+  D.nTiles = (p->K + D.S - 1) / D.S;
+  D.GT = (D.nTiles + 63) / 64;
+  if (D.GT < 32) D.GT = 32;
+  D.nGroups = (D.nTiles + D.GT - 1) / D.GT;
+  D.nscl = D.GT > D.nGroups ? D.GT : D.nGroups;
+  D.dt = (float)p->dt;
+  D.h_eps = (float)p->h_eps;
+  D.gamma_bas_f = (float)p->gamma_bas;
+  D.R_B = (float)p->R_B;
+  D.C_coll = (float)p->C_coll;
+  D.ln_mu = (float)p->ln_mu;
+  D.ln_sigma = (float)p->ln_sigma;
+  for (int d = 0; d < 2; ++d) {
+    D.umin[d] = (float)p->u_min[d];
+    D.umax[d] = (float)p->u_max[d];
+    D.umin_d[d] = p->u_min[d];
+    D.umax_d[d] = p->u_max[d];
+  }
+  for (int d = 0; d < kMaxN; ++d) {
+    D.Q[d] = d < c->n ? (float)p->Q[d] : 0.0f;
+    D.Qf[d] = d < c->n ? (float)p->Qf[d] : 0.0f;
+    D.x_goal[d] = d < c->n ? p->x_goal[d] : 0.0;
+  }
+  for (int i = 0; i < 2 * kMaxShape; ++i)
+    D.shape[i] = i < 2 * p->n_shape ? (float)p->shape[i] : 0.0f;
+  D.g = (float)p->gravity;
+  D.inv_mass = p->model == MPPI_QUAD2D ? (float)(1.0 / p->mass) : 0.0f;
+  D.arm_over_I = p->model == MPPI_QUAD2D ? (float)(p->arm / p->inertia) : 0.0f;
+  D.lambda = p->lambda;
+  D.inv_lambda = 1.0 / p->lambda;
+  D.mu_coarse = p->mu_coarse;
+  D.gamma_ctrl = p->gamma_ctrl;
+  D.gamma_bas = p->gamma_bas;
+  for (int i = 0; i < 4; ++i) D.sigma[i] = p->sigma[i];
+  D.key0 = (uint32_t)(p->seed & 0xffffffffull);
+  D.key1 = (uint32_t)(p->seed >> 32);
+  D.U = c->d_U;
+  D.cU = c->d_cU;
+  D.cA = c->d_cA;
+  D.st = c->d_st;
+  D.obst = c->d_obst;
+  D.x0 = c->d_in;
+  D.xref = c->d_in + c->n;
+  D.part = c->d_part;
+  D.part_rz = c->d_part_rz;
+  D.gpart = c->d_gpart;
+  D.gpart_rz = c->d_gpart_rz;
+  D.counters = c->d_cnt;
+  D.costs = c->d_costs;
+  D.coll = c->d_coll;
+  D.Ustar = c->d_Ustar;
+}
+
+int check_status(mppi_ctx* c) {
+  if (c->h_st->status == kStatusTimeout)
+    return fail(MPPI_ETIMEOUT, "a bounded device wait (obstacle staging) expired");
+  return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mppi_last_error(void) { return g_err; }
+
+int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_tiling* tiling,
+                      mppi_ctx** out) {
+  if (!out) return fail(MPPI_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  if (u_init && !finite_all(u_init, 2 * p->T)) return fail(MPPI_EINVAL, "non-finite u_init");
+  mppi_ctx* c = new (std::nothrow) mppi_ctx();
+  if (!c) return fail(MPPI_ENOMEM, "host allocation failed");
+  c->p = *p;
+  c->n = state_dim(p->model);
+  rc = choose_tiling(p, tiling, 0, &c->tl, &c->smem);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  const int T = p->T, K = p->K, n = c->n;
+  const int nTiles = (K + c->tl.samples_per_cta - 1) / c->tl.samples_per_cta;
+  int GT = (nTiles + 63) / 64;
+  if (GT < 32) GT = 32;
+  const int nGroups = (nTiles + GT - 1) / GT;
+#define ALLOC(ptr, bytes)                                                          \
+  do {                                                                             \
+    if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                      \
+      cudaGetLastError();                                                          \
+      free_ctx(c);                                                                 \
+      return fail(MPPI_ENOMEM, "cudaMalloc of %zu bytes failed", (size_t)(bytes)); \
+    }                                                                              \
+  } while (0)
+  ALLOC(c->d_U, sizeof(double) * 2 * T);
+  ALLOC(c->d_cU, sizeof(float2) * T);
+  ALLOC(c->d_cA, sizeof(float2) * T);
+  ALLOC(c->d_st, sizeof(DevState));
+  ALLOC(c->d_obst, 16);
+  c->Jcap = 0;
+  ALLOC(c->d_in, sizeof(double) * (n + (T + 1) * n));
+  ALLOC(c->d_part, sizeof(float) * (size_t)nTiles * 2 * T);
+  ALLOC(c->d_part_rz, sizeof(double2) * nTiles);
+  ALLOC(c->d_gpart, sizeof(float) * (size_t)nGroups * 2 * T);
+  ALLOC(c->d_gpart_rz, sizeof(double2) * nGroups);
+  ALLOC(c->d_cnt, sizeof(unsigned) * (nGroups + 1));
+  ALLOC(c->d_costs, sizeof(double) * K);
+  ALLOC(c->d_coll, K);
+  ALLOC(c->d_Ustar, sizeof(double) * 2 * T);
+  ALLOC(c->d_w, sizeof(double) * K);
+#undef ALLOC
+  if (cudaMallocHost((void**)&c->h_in, sizeof(double) * (n + (T + 1) * n)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_st, sizeof(DevState)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_U, sizeof(double) * 2 * T) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(c);
+    return fail(MPPI_ENOMEM, "pinned host allocation failed");
+  }
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming) != cudaSuccess) {
+    free_ctx(c);
+    return fail(MPPI_ECUDA, "stream/event creation failed");
+  }
+  c->last = c->own;
+  fill_desc(c);
+  c->fn = pick_kernel(p->model, c->tl.positions_per_thread);
+  if (cudaFuncSetAttribute(c->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_optin()) !=
+      cudaSuccess) {
+    free_ctx(c);
+    return fail(MPPI_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  // initial state: U, S_e = mu ln(e + 0) (Eq. 10 with C_B = 0), first call
+  DevState st;
+  memset(&st, 0, sizeof(st));
+  st.S_e = p->mu_coarse > 0 ? p->mu_coarse : 1.0;
+  st.first = 1;
+  double* U0 = c->h_U;
+  for (int i = 0; i < 2 * T; ++i) U0[i] = u_init ? u_init[i] : 0.0;
+  if (cudaMemcpy(c->d_U, U0, sizeof(double) * 2 * T, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_st, &st, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->d_cnt, 0, sizeof(unsigned) * (nGroups + 1)) != cudaSuccess) {
+    free_ctx(c);
+    return fail(MPPI_ECUDA, "initial upload failed");
+  }
+  prep_kernel<<<1, 256, 0, c->own>>>(c->D);
+  if (cudaStreamSynchronize(c->own) != cudaSuccess) {
+    free_ctx(c);
+    return fail(MPPI_ECUDA, "prep kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  *out = c;
+  return MPPI_OK;
+}
+
+int mppi_create(const mppi_params* p, const double* u_init, mppi_ctx** out) {
+  return mppi_create_tiled(p, u_init, nullptr, out);
+}
+
+int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (J < 0 || J > MPPI_MAX_OBSTACLES)
+    return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
+  if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
+  for (int j = 0; j < J; ++j) {
+    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
+    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+  }
+  mppi_tiling t;
+  int smem = 0;
+  int rc = choose_tiling(&c->p, &c->tl, J, &t, &smem);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->last));
+  const size_t bytes = (size_t)align_up(24 * (J > 0 ? J : 1), 16);
+  if (J > c->Jcap) {
+    double* nb = nullptr;
+    if (cudaMalloc((void**)&nb, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPPI_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    cudaFree(c->d_obst);
+    c->d_obst = nb;
+    c->Jcap = J;
+  }
+  if (J > 0) {
+    CK(cudaMemset(c->d_obst, 0, bytes));
+    CK(cudaMemcpy(c->d_obst, cxcyr, sizeof(double) * 3 * J, cudaMemcpyHostToDevice));
+  }
+  c->tl = t;
+  c->smem = smem;
+  c->D.TC = t.chunk_steps;
+  c->D.J = J;
+  c->D.obst = c->d_obst;
+  return MPPI_OK;
+}
+
+int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref, void* stream) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!d_x0 || !d_xref) return fail(MPPI_EINVAL, "device x0 / xref must not be NULL");
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
+  c->fn<<<c->D.nTiles, c->tl.threads, c->smem, s>>>(c->D, d_x0, d_xref);
+  CK(cudaGetLastError());
+  c->last = s;
+  c->stepped = true;
+  return MPPI_OK;
+}
+
+int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!x0) return fail(MPPI_EINVAL, "x0 is NULL");
+  const int n = c->n, T = c->p.T;
+  if (!finite_all(x0, n)) return fail(MPPI_EINVAL, "x0 is not finite");
+  if (xref && !finite_all(xref, (T + 1) * n)) return fail(MPPI_EINVAL, "xref is not finite");
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
+  if (c->in_ev_pending) CK(cudaEventSynchronize(c->in_ev));  // staging buffer free again
+  memcpy(c->h_in, x0, sizeof(double) * n);
+  if (xref) {
+    memcpy(c->h_in + n, xref, sizeof(double) * (T + 1) * n);
+  } else {
+    for (int t = 0; t <= T; ++t) memcpy(c->h_in + n + t * n, c->p.x_goal, sizeof(double) * n);
+  }
+  CK(cudaMemcpyAsync(c->d_in, c->h_in, sizeof(double) * (n + (T + 1) * n), cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(c->in_ev, s));
+  c->in_ev_pending = true;
+  return mppi_step_device(c, c->d_in, c->d_in + n, s);
+}
+
+int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!c->stepped) return fail(MPPI_ESTATE, "no step has run");
+  CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, c->last));
+  if (U) CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost, c->last));
+  CK(cudaStreamSynchronize(c->last));
+  int rc = check_status(c);
+  if (rc) return rc;
+  if (u0) {
+    u0[0] = c->h_st->u0[0];
+    u0[1] = c->h_st->u0[1];
+  }
+  if (U) memcpy(U, c->h_U, sizeof(double) * 2 * c->p.T);
+  return MPPI_OK;
+}
+
+int mppi_get_debug(mppi_ctx* c, double* costs, uint8_t* collided, double* weights, double* Ustar,
+                   double* scalars) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!c->stepped) return fail(MPPI_ESTATE, "no step has run");
+  const int K = c->p.K, T = c->p.T;
+  cudaStream_t s = c->last;
+  if (weights) {
+    weights_kernel<<<(K + 255) / 256, 256, 0, s>>>(c->d_costs, K, c->d_st, 1.0 / c->p.lambda, c->d_w);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (costs) CK(cudaMemcpy(costs, c->d_costs, sizeof(double) * K, cudaMemcpyDeviceToHost));
+  if (collided) CK(cudaMemcpy(collided, c->d_coll, K, cudaMemcpyDeviceToHost));
+  if (weights) CK(cudaMemcpy(weights, c->d_w, sizeof(double) * K, cudaMemcpyDeviceToHost));
+  if (Ustar) CK(cudaMemcpy(Ustar, c->d_Ustar, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost));
+  if (scalars) {
+    const DevState& st = *c->h_st;
+    scalars[0] = st.rho;
+    scalars[1] = st.Z;
+    scalars[2] = st.CB_star;
+    scalars[3] = st.S_e;
+    scalars[4] = st.beta_used;
+    scalars[5] = st.beta_d;
+    scalars[6] = st.S_e_used;
+    scalars[7] = (double)st.iter;
+  }
+  return check_status(c);
+}
+
+int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (h2d) *h2d = sizeof(double) * (uint64_t)(c->n + (c->p.T + 1) * c->n);
+  if (d2h) *d2h = sizeof(DevState);
+  return MPPI_OK;
+}
+
+int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (t) *t = c->tl;
+  if (n_ctas) *n_ctas = c->D.nTiles;
+  return MPPI_OK;
+}
+
+int mppi_get_state(mppi_ctx* c, double* U, double* S_e, double* beta, int32_t* first,
+                   uint64_t* iter) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  CK(cudaStreamSynchronize(c->last));
+  CK(cudaMemcpy(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  if (U) CK(cudaMemcpy(U, c->d_U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost));
+  if (S_e) *S_e = c->h_st->S_e;
+  if (beta) *beta = c->h_st->beta;
+  if (first) *first = c->h_st->first;
+  if (iter) *iter = c->h_st->iter;
+  return MPPI_OK;
+}
+
+int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta, int32_t first,
+                   uint64_t iter) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!U || !finite_all(U, 2 * c->p.T)) return fail(MPPI_EINVAL, "U missing or not finite");
+  if (!std::isfinite(S_e) || !(S_e > 0) || !std::isfinite(beta))
+    return fail(MPPI_EINVAL, "S_e must be finite and > 0, beta finite");
+  CK(cudaStreamSynchronize(c->last));
+  CK(cudaMemcpy(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  DevState st = *c->h_st;
+  st.S_e = S_e;
+  st.beta = beta;
+  st.first = first ? 1 : 0;
+  st.iter = iter;
+  st.status = 0;
+  CK(cudaMemcpy(c->d_U, U, sizeof(double) * 2 * c->p.T, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_st, &st, sizeof(DevState), cudaMemcpyHostToDevice));
+  prep_kernel<<<1, 256, 0, c->own>>>(c->D);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->own));
+  return MPPI_OK;
+}
+
+int mppi_debug_draws(const mppi_params* p, double S_e, uint64_t iter, int32_t K, int32_t T,
+                     uint32_t* raw, float* du) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (K < 1 || T < 1 || (long)K * T > (1L << 26)) return fail(MPPI_EINVAL, "K*T out of range");
+  if (!(S_e > 0)) return fail(MPPI_EINVAL, "S_e must be > 0");
+  double a = S_e * p->sigma[0], c = S_e * p->sigma[2], d = S_e * p->sigma[3];
+  double l00 = std::sqrt(a > 0 ? a : 0.0);
+  double l10 = l00 > 0 ? c / l00 : 0.0;
+  double r = d - l10 * l10;
+  double l11 = std::sqrt(r > 0 ? r : 0.0);
+  const size_t N = (size_t)K * T;
+  uint32_t* d_raw = nullptr;
+  float* d_du = nullptr;
+  CK(cudaMalloc((void**)&d_raw, N * 16));
+  if (cudaMalloc((void**)&d_du, N * 8) != cudaSuccess) {
+    cudaFree(d_raw);
+    return fail(MPPI_ENOMEM, "cudaMalloc failed");
+  }
+  draws_kernel<<<(unsigned)((N + 255) / 256), 256>>>(
+      K, T, (uint32_t)(p->seed & 0xffffffffull), (uint32_t)(p->seed >> 32),
+      (uint32_t)(iter & 0xffffffffull), (uint32_t)(iter >> 32), (float)l00, (float)l10, (float)l11,
+      (float)p->ln_mu, (float)p->ln_sigma, d_raw, d_du);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && raw) e = cudaMemcpy(raw, d_raw, N * 16, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && du) e = cudaMemcpy(du, d_du, N * 8, cudaMemcpyDeviceToHost);
+  cudaFree(d_raw);
+  cudaFree(d_du);
+  if (e != cudaSuccess) return fail(MPPI_ECUDA, "draws failed: %s", cudaGetErrorString(e));
+  return MPPI_OK;
+}
+
+int mppi_destroy(mppi_ctx* c) {
+  free_ctx(c);
+  return MPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA step (through the C ABI) against the CPU FP64 oracle,
+element by element, on the same seeded inputs.
+
+Tolerances: per-sample cost-to-go within 1e-4 relative (relative to
+max(|S|, 1)), the updated control sequence U* within 1e-5 absolute, the set
+of collided samples identical wherever the oracle's min h is farther than
+H_MARGIN from zero (closer samples are reported, not asserted).  Philox words
+are compared bit for bit."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2504_06437_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-4
+U_ATOL = 1e-5
+H_MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06437_gb300 import binding
+    binding.build()
+    binding.load()
+    return binding
+
+
+def compare_step(ro, dbg, u0, U_next, label=""):
+    S_o, S_g = ro["costs"], dbg["costs"]
+    rel = np.abs(S_g - S_o) / np.maximum(np.abs(S_o), 1.0)
+    assert rel.max() <= COST_RTOL, f"{label} cost rel err {rel.max():.3e} at k={rel.argmax()}"
+    sure = np.abs(ro["minh"]) > H_MARGIN
+    mism = np.nonzero((ro["coll"] != dbg["coll"]) & sure)[0]
+    assert mism.size == 0, f"{label} collided set differs at {mism[:10]}"
+    np.testing.assert_allclose(dbg["Ustar"], ro["Ustar"], rtol=0, atol=U_ATOL, err_msg=label)
+    np.testing.assert_allclose(u0, ro["u0"], rtol=0, atol=U_ATOL, err_msg=label)
+    np.testing.assert_allclose(U_next, ro["U_next"], rtol=0, atol=U_ATOL, err_msg=label)
+    assert abs(dbg["weights"].sum() - 1.0) < 1e-9
+    np.testing.assert_allclose(dbg["weights"], ro["weights"], rtol=0, atol=1e-4, err_msg=label)
+    assert dbg["beta_used"] == pytest.approx(ro["beta_used"], rel=1e-5, abs=1e-6)
+    assert dbg["beta_d"] == pytest.approx(ro["beta_d"], rel=1e-5, abs=1e-6)
+    assert dbg["CB_star"] == pytest.approx(ro["CB_star"], rel=1e-4, abs=1e-4)
+    assert dbg["S_e_next"] == pytest.approx(ro["S_e_next"], rel=1e-5)
+    return dict(cost_rel=float(rel.max()),
+                U_abs=float(np.abs(dbg["Ustar"] - ro["Ustar"]).max()),
+                w_abs=float(np.abs(dbg["weights"] - ro["weights"]).max()))
+
+
+def run_pair(gpu, orc, world, steps=1, tiling=None, u_init=None, x_seq=None):
+    """Run the oracle and the GPU side by side for `steps` iterations; the
+    plant is advanced with the oracle's u0 so both see the same x0."""
+    p = world.params
+    ctl = orc.new_controller(p, u_init)
+    errs = []
+    with gpu.Controller(p, u_init=u_init, tiling=tiling) as g:
+        g.set_obstacles(world.obstacles)
+        x = world.x_start.copy()
+        for i in range(steps):
+            xref = world.reference(x)
+            ro = orc.step(p, world.obstacles, x, xref, ctl)
+            g.step(x, xref)
+            u0, U_next = g.get_control(want_U=True)
+            dbg = g.get_debug()
+            errs.append(compare_step(ro, dbg, u0, U_next, label=f"{world.name} step {i}"))
+            x = orc.dynamics(p, x, ro["u0"])
+    return errs
+
+
+def _small(world_fn, seed=0, **over):
+    w = world_fn(seed)
+    w.params.update(over)
+    return w
+
+
+def test_philox_words_bit_exact(gpu, orc):
+    p = W.base_params(W.UNICYCLE, K=8, T=4, dt=0.05, seed=0x123456789ABCDEF)
+    raw, _ = gpu.debug_draws(p, 0.4, (7 << 32) + 3, 37, 11)
+    it = (7 << 32) + 3
+    key = [p["seed"] & 0xFFFFFFFF, p["seed"] >> 32]
+    for k in range(37):
+        for t in range(11):
+            ref = orc.philox4x32_10([k, t, it & 0xFFFFFFFF, it >> 32], key)
+            np.testing.assert_array_equal(raw[k, t], ref)
+
+
+@pytest.mark.parametrize("sig", [[0.5, 0.0, 0.0, 0.5], [0.5, 0.2, 0.2, 0.3]])
+def test_nln_draws_match_oracle(gpu, orc, sig):
+    p = W.base_params(W.UNICYCLE, K=8, T=4, dt=0.05, seed=11)
+    p["sigma"] = sig
+    _, du = gpu.debug_draws(p, 0.7, 5, 64, 30)
+    ref, _ = orc.noise_batch(p, 0.7, 64, 30, 5)
+    np.testing.assert_allclose(du, ref, rtol=2e-6, atol=2e-6)
+
+
+def test_unicycle_small_closed_loop(gpu, orc):
+    """Config 1 (K=256, T=30, 10 obstacles), five receding-horizon steps."""
+    run_pair(gpu, orc, W.unicycle_small(0), steps=5)
+
+
+def test_quad_ragged_tiles(gpu, orc):
+    """Planar quadrotor, K=1000 (ragged last tile), T=50, 40 obstacles, 7 shape points."""
+    w = W.quad2d(1, K=1000, T=50)
+    run_pair(gpu, orc, w, steps=3)
+
+
+@pytest.mark.parametrize("tiling", [
+    dict(samples_per_cta=32, threads=64, positions_per_thread=4, chunk_steps=0),
+    dict(samples_per_cta=7, threads=512, positions_per_thread=16, chunk_steps=3),
+    dict(samples_per_cta=1, threads=128, positions_per_thread=8, chunk_steps=0),
+    dict(samples_per_cta=20, threads=256, positions_per_thread=8, chunk_steps=11),
+])
+def test_tilings_agree_with_oracle(gpu, orc, tiling):
+    w = W.quad2d(2, K=777, T=23)
+    run_pair(gpu, orc, w, steps=2, tiling=tiling)
+    w = W.unicycle_small(2)
+    w.params.update(K=999, T=41)
+    run_pair(gpu, orc, w, steps=2, tiling=tiling)
+
+
+def test_no_obstacles(gpu, orc):
+    w = W.unicycle_small(3)
+    w.obstacles = np.zeros((0, 3))
+    errs = run_pair(gpu, orc, w, steps=2)
+    assert errs
+
+
+def test_single_sample_single_step(gpu, orc):
+    w = W.unicycle_small(4)
+    w.params.update(K=1, T=1)
+    run_pair(gpu, orc, w, steps=3)
+
+
+def test_many_collisions(gpu, orc):
+    """Obstacles placed on the straight path: many samples collide."""
+    w = W.unicycle_small(5)
+    line = np.linspace(1.3, 2.5, 6)
+    w.obstacles = np.array([[x, x, 0.25] for x in line])
+    w.params.update(K=2048)
+    p = w.params
+    ctl = orc.new_controller(p, np.tile([1.5, 0.0], (p["T"], 1)))
+    with gpu.Controller(p, u_init=np.tile([1.5, 0.0], (p["T"], 1))) as g:
+        g.set_obstacles(w.obstacles)
+        x = w.x_start
+        xref = w.reference(x)
+        ro = orc.step(p, w.obstacles, x, xref, ctl)
+        g.step(x, xref)
+        u0, Un = g.get_control(want_U=True)
+        compare_step(ro, g.get_debug(), u0, Un, "collisions")
+    assert 0 < ro["coll"].sum() < p["K"]
+
+
+def test_max_sizes(gpu, orc):
+    """T = 256 (limit), 4096 obstacles (limit), 8 shape points."""
+    w = W.unicycle_small(6)
+    g = W.rng(6)
+    w.obstacles = W.obstacle_field(g, 4096, (-40, -40), (50, 50), 0.05, 0.3,
+                                   keep_clear=(w.x_start, w.goal))
+    w.params.update(K=96, T=256, shape=np.array([[0.2 * math.cos(a), 0.2 * math.sin(a)]
+                                                  for a in np.linspace(0, 2 * math.pi, 8, endpoint=False)]))
+    run_pair(gpu, orc, w, steps=1)
+
+
+def test_quad_full_size_bench_config(gpu, orc):
+    """The benchmark workload (K=4096, T=50, 40 obstacles, 7 shape points) in
+    the launch shape the benchmark uses, all samples compared."""
+    run_pair(gpu, orc, W.quad2d(0), steps=2)
+
+
+def test_stress_config_sampled(gpu, orc):
+    """K=65536, T=100, 200 obstacles: many tile groups.  Costs of 512 sampled
+    samples against the oracle; weights sum to one; U* within the box."""
+    w = W.unicycle_stress(0)
+    p = w.params
+    ctl = orc.new_controller(p)
+    with gpu.Controller(p) as g:
+        g.set_obstacles(w.obstacles)
+        x = w.x_start
+        xref = w.reference(x)
+        g.step(x, xref)
+        g.get_control()
+        dbg = g.get_debug()
+    ks = np.unique(np.concatenate([np.arange(0, p["K"], 131), [p["K"] - 1],
+                                   np.argsort(dbg["costs"])[:32]]))
+    ro = orc.sample_costs(p, w.obstacles, x, xref, ctl, ks)
+    rel = np.abs(dbg["costs"][ks] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
+    assert rel.max() <= COST_RTOL
+    sure = np.abs(ro["minh"]) > H_MARGIN
+    assert np.all((ro["coll"] == dbg["coll"][ks]) | ~sure)
+    assert abs(dbg["weights"].sum() - 1.0) < 1e-9
+    assert np.all(dbg["Ustar"] >= np.array(p["u_min"]) - 1e-12)
+    assert np.all(dbg["Ustar"] <= np.array(p["u_max"]) + 1e-12)
+
+
+def test_checkpoint_resume_bit_exact(gpu, orc):
+    w = W.quad2d(7, K=512, T=30)
+    p = w.params
+    x = w.x_start
+    xref = w.reference(x)
+    with gpu.Controller(p) as a, gpu.Controller(p) as b:
+        a.set_obstacles(w.obstacles)
+        b.set_obstacles(w.obstacles)
+        a.step(x, xref)
+        a.get_control()
+        st = a.get_state()
+        b.set_state(st["U"], st["S_e"], st["beta"], st["first"], st["iter"])
+        a.step(x, xref)
+        ua = a.get_control()
+        b.step(x, xref)
+        ub = b.get_control()
+        np.testing.assert_array_equal(ua, ub)
+        np.testing.assert_array_equal(a.get_debug()["costs"], b.get_debug()["costs"])
+
+
+def test_repeatable(gpu, orc):
+    w = W.quad2d(8, K=2000, T=40)
+    outs = []
+    for _ in range(2):
+        with gpu.Controller(w.params) as g:
+            g.set_obstacles(w.obstacles)
+            g.step(w.x_start, w.reference(w.x_start))
+            outs.append((g.get_control(), g.get_debug()["costs"]))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_error_paths(gpu):
+    w = W.unicycle_small(0)
+    with gpu.Controller(w.params) as g:
+        with pytest.raises(gpu.MppiError) as e:
+            g.get_control()
+        assert e.value.code == gpu.MPPI_ESTATE
+        bad = w.obstacles.copy()
+        bad[0, 2] = -1.0
+        with pytest.raises(gpu.MppiError) as e:
+            g.set_obstacles(bad)
+        assert e.value.code == gpu.MPPI_EINVAL
+        bad[0] = [np.nan, 0, 1]
+        with pytest.raises(gpu.MppiError):
+            g.set_obstacles(bad)
+        with pytest.raises(gpu.MppiError):
+            g.set_obstacles(np.zeros((5000, 3)))
+        with pytest.raises(gpu.MppiError):
+            g.step([np.nan, 0, 0])
+        g.set_obstacles(w.obstacles)
+        g.step(w.x_start)          # xref NULL -> goal repeated
+        u0 = g.get_control()
+        assert np.all(np.isfinite(u0))
