@@ -255,7 +255,11 @@ def main():
     d_in = torch.tensor(np.concatenate([x0, xref.ravel()]), dtype=torch.float64, device="cuda")
     d_x0 = d_in.data_ptr()
     d_xref = d_x0 + 8 * n
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it, the events and the L2
+    # flush are recorded on it (torch's default stream would be handle 0,
+    # which the C ABI reads as "the context's own stream")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):

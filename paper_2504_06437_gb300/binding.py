@@ -47,7 +47,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["nvcc", *NVCC_FLAGS, "-o", tmp, *[os.path.join(_HERE, s) for s in _SOURCES]]
+    extra = os.environ.get("DBASMPPI_NVCC_EXTRA", "").split()
+    cmd = ["nvcc", *NVCC_FLAGS, *extra, "-o", tmp, *[os.path.join(_HERE, s) for s in _SOURCES]]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

@@ -40,16 +40,17 @@ __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ CtrlD
                                                    const double* __restrict__ xref) {
   extern __shared__ __align__(16) char smem[];
   __shared__ TileScratch ts;
-  if (threadIdx.x == 0) {
-    mbar_init(&ts.mbar);
-    ts.mbar_phase = 0u;
-  }
+  if (threadIdx.x == 0) mbar_init(&ts.mbar);
   __syncthreads();
-  run_tile<MODEL, NPOS>(D, blockIdx.x, x0, xref, smem, ts);
+  uint32_t phase = 0u;
+  run_tile<MODEL, NPOS>(D, blockIdx.x, x0, xref, smem, ts, phase);
 }
 
-__global__ void prep_kernel(const __grid_constant__ CtrlDesc D) {
+// Constants of the controller (init != 0, at creation) and the per-step
+// constants of its current state.
+__global__ void prep_kernel(const __grid_constant__ CtrlDesc D, int init) {
   __shared__ double red[64];
+  if (init) init_constants(D, threadIdx.x, blockDim.x);
   prep_constants(D, red, threadIdx.x, blockDim.x);
 }
 
@@ -76,13 +77,30 @@ using StepFn = void (*)(CtrlDesc, const double*, const double*);
 
 StepFn pick_kernel(int model, int npos) {
   if (model == MPPI_UNICYCLE) {
-    if (npos == 4) return step_kernel<0, 4>;
+    if (npos == 14) return step_kernel<0, 14>;
     if (npos == 16) return step_kernel<0, 16>;
     return step_kernel<0, 8>;
   }
-  if (npos == 4) return step_kernel<1, 4>;
+  if (npos == 14) return step_kernel<1, 14>;
   if (npos == 16) return step_kernel<1, 16>;
   return step_kernel<1, 8>;
+}
+
+// World points a barrier thread holds: whole units of P points each; the
+// instantiated sizes are 8, 14 and 16, picked to waste the fewest slots.
+int pick_npos(int P) {
+  const int opts[3] = {8, 14, 16};
+  int best = 16;
+  double best_waste = 2.0;
+  for (int o : opts) {
+    if (o < P) continue;
+    double waste = (double)(o - (o / P) * P) / o;
+    if (waste < best_waste - 1e-12) {
+      best_waste = waste;
+      best = o;
+    }
+  }
+  return best;
 }
 
 int state_dim(int model) { return model == MPPI_QUAD2D ? 6 : 3; }
@@ -138,11 +156,18 @@ int num_sms() {
   return g_num_sms;
 }
 
+// Largest dynamic shared memory a step kernel may request: the opt-in
+// per-block maximum less the kernel's static shared memory.
 int max_smem_optin() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v > 0 ? v : 48 * 1024;
+  if (v <= 0) v = 48 * 1024;
+  cudaFuncAttributes fa;
+  size_t stat = 0;
+  if (cudaFuncGetAttributes(&fa, step_kernel<1, 16>) == cudaSuccess) stat = fa.sharedSizeBytes;
+  else cudaGetLastError();
+  return v - (int)align_up((int)stat + 64, 128);
 }
 
 }  // namespace
@@ -160,6 +185,7 @@ struct mppi_ctx {
   double* d_U = nullptr;
   float2* d_cU = nullptr;
   float2* d_cA = nullptr;
+  float* d_cw = nullptr;
   DevState* d_st = nullptr;
   double* d_obst = nullptr;
   double* d_in = nullptr;  // x0 (n) then xref ((T+1) n)
@@ -190,6 +216,7 @@ void free_ctx(mppi_ctx* c) {
   cudaFree(c->d_U);
   cudaFree(c->d_cU);
   cudaFree(c->d_cA);
+  cudaFree(c->d_cw);
   cudaFree(c->d_st);
   cudaFree(c->d_obst);
   cudaFree(c->d_in);
@@ -227,12 +254,15 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
   if (t.threads <= 0) t.threads = 256;
   if (t.threads != 64 && t.threads != 128 && t.threads != 256 && t.threads != 512)
     return fail(MPPI_EINVAL, "threads must be 64, 128, 256 or 512");
-  if (t.positions_per_thread <= 0) t.positions_per_thread = 8;
-  if (t.positions_per_thread != 4 && t.positions_per_thread != 8 && t.positions_per_thread != 16)
-    return fail(MPPI_EINVAL, "positions_per_thread must be 4, 8 or 16");
-  const int SP = t.samples_per_cta * p->n_shape;
+  if (t.positions_per_thread <= 0) t.positions_per_thread = pick_npos(p->n_shape);
+  if (t.positions_per_thread != 8 && t.positions_per_thread != 14 && t.positions_per_thread != 16)
+    return fail(MPPI_EINVAL, "positions_per_thread must be 8, 14 or 16");
+  if (t.positions_per_thread < p->n_shape)
+    return fail(MPPI_EINVAL, "positions_per_thread must be >= n_shape");
   if (t.chunk_steps <= 0) {
-    int tc = (t.threads * t.positions_per_thread + SP - 1) / SP;
+    // one round of barrier units per chunk: threads x (NPOS / P) units
+    int units = t.threads * (t.positions_per_thread / p->n_shape);
+    int tc = (units + t.samples_per_cta - 1) / t.samples_per_cta;
     t.chunk_steps = tc < 1 ? 1 : tc;
   }
   if (t.chunk_steps > p->T) t.chunk_steps = p->T;
@@ -243,7 +273,8 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
   const int nGroups = (nTiles + GT - 1) / GT;
   const int nscl = GT > nGroups ? GT : nGroups;
   for (;;) {
-    SmemLayout L = smem_layout(p->T, t.samples_per_cta, t.chunk_steps, p->n_shape, J, n, nscl);
+    SmemLayout L =
+        smem_layout(p->T, t.samples_per_cta, t.chunk_steps, p->n_shape, J, n, nscl, t.threads / 32);
     if (L.total <= limit) {
       *smem_out = L.total;
       break;
@@ -305,12 +336,31 @@ void fill_desc(mppi_ctx* c) {
   D.mu_coarse = p->mu_coarse;
   D.gamma_ctrl = p->gamma_ctrl;
   D.gamma_bas = p->gamma_bas;
+  D.R_B_d = p->R_B;
   for (int i = 0; i < 4; ++i) D.sigma[i] = p->sigma[i];
+  {
+    // chol(Sigma) and gamma Sigma^-1 (PSD checked by validate; inverse only
+    // needed, and only defined, when gamma_ctrl != 0)
+    const double* S = p->sigma;
+    double l00 = std::sqrt(S[0] > 0 ? S[0] : 0.0);
+    double l10 = l00 > 0 ? S[2] / l00 : 0.0;
+    double r = S[3] - l10 * l10;
+    D.Lsig[0] = l00;
+    D.Lsig[1] = l10;
+    D.Lsig[2] = std::sqrt(r > 0 ? r : 0.0);
+    double det = S[0] * S[3] - S[1] * S[2];
+    double gi = p->gamma_ctrl != 0 ? p->gamma_ctrl / det : 0.0;
+    D.Sinv[0] = gi * S[3];
+    D.Sinv[1] = -gi * S[1];
+    D.Sinv[2] = -gi * S[2];
+    D.Sinv[3] = gi * S[0];
+  }
   D.key0 = (uint32_t)(p->seed & 0xffffffffull);
   D.key1 = (uint32_t)(p->seed >> 32);
   D.U = c->d_U;
   D.cU = c->d_cU;
   D.cA = c->d_cA;
+  D.cw = c->d_cw;
   D.st = c->d_st;
   D.obst = c->d_obst;
   D.x0 = c->d_in;
@@ -369,6 +419,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   ALLOC(c->d_U, sizeof(double) * 2 * T);
   ALLOC(c->d_cU, sizeof(float2) * T);
   ALLOC(c->d_cA, sizeof(float2) * T);
+  ALLOC(c->d_cw, sizeof(float) * T);
   ALLOC(c->d_st, sizeof(DevState));
   ALLOC(c->d_obst, 16);
   c->Jcap = 0;
@@ -416,7 +467,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
     free_ctx(c);
     return fail(MPPI_ECUDA, "initial upload failed");
   }
-  prep_kernel<<<1, 256, 0, c->own>>>(c->D);
+  prep_kernel<<<1, 256, 0, c->own>>>(c->D, 1);
   if (cudaStreamSynchronize(c->own) != cudaSuccess) {
     free_ctx(c);
     return fail(MPPI_ECUDA, "prep kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -586,7 +637,7 @@ int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta, int32_
   st.status = 0;
   CK(cudaMemcpy(c->d_U, U, sizeof(double) * 2 * c->p.T, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->d_st, &st, sizeof(DevState), cudaMemcpyHostToDevice));
-  prep_kernel<<<1, 256, 0, c->own>>>(c->D);
+  prep_kernel<<<1, 256, 0, c->own>>>(c->D, 0);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->own));
   return MPPI_OK;

@@ -9,10 +9,12 @@
 //   warp 0      (lane = sample) clamps v = u + du, steps the dynamics (Eq. 1,
 //               8), accumulates the stage and control costs (Eq. 9), and runs
 //               the DBaS recursion (Eq. 7) of the previous chunk;
-//   all warps   evaluate the fused barrier sum over every (step, sample,
-//               shape point) position and every obstacle (Eq. 5, 13/15): each
-//               thread keeps NPOS world points in registers and streams the
-//               obstacle set from shared memory (broadcast reads).
+//   all warps   evaluate the fused barrier sum over every (step, sample)
+//               unit, its P shape points and every obstacle (Eq. 5, 13/15):
+//               each thread keeps whole units (NPOS world points) in
+//               registers, streams the obstacle set from shared memory
+//               (broadcast reads) and sums each unit's points exactly into a
+//               float pair.
 // After the horizon the tile forms its own min-shifted exponentiated weights
 // and weighted perturbation sums (the numerator and denominator of Eq. 4
 // relative to the tile's own minimum).  Tiles are combined by a two-level
@@ -21,12 +23,21 @@
 // runs the nominal rollout of U* for C_B (Algorithm 1), sets S_e (Eq. 10) and
 // shifts the sequence.
 //
+// The DBaS recursion of Eq. 7, w_t = b_t + gamma (w_{t-1} - beta_d), is
+// linear, so its cost sum is evaluated in unrolled form:
+//   sum_{t=1..T} w_t = sum_s c_s b_s + beta_0 g1 - gamma beta_d csum,
+//   c_s = (1 - gamma^(T-s+1)) / (1 - gamma),  g1 = gamma (1 - gamma^T) / (1 - gamma),
+//   csum = sum_s c_s,
+// which removes the rounding of the running state w; the sample-independent
+// part is formed once in FP64.
+//
 // Precision: the rollout runs in FP32 in a frame whose origin is the
 // measured position (obstacles and reference are moved into it in FP64 then
 // rounded), so coordinates stay small; the per-sample cost is accumulated as
-// an unevaluated float pair (TwoSum), the part of the control cost common to
-// all samples is added in FP64, the normaliser and the tile minima are FP64,
-// and the cross-tile sums of weighted perturbations are compensated FP32.
+// an unevaluated float pair (TwoSum / TwoProd), the parts of the cost common
+// to all samples are added in FP64, the normaliser and the tile minima are
+// FP64, and the cross-tile sums of weighted perturbations are compensated
+// FP32.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -50,6 +61,7 @@ struct DevState {
   double S_e_used;   // last step: exploration rate of the draws
   double u0[2];      // last step: u*_0
   double C0;         // sum_t gamma u_t^T (S_e Sigma)^-1 u_t of the next step
+  double csum, g1;   // DBaS unrolling constants (see above)
   float L00, L10, L11, pad;  // chol(S_e Sigma) of the next step
   unsigned long long iter;  // Philox counter words 2..3
   int first;         // 1 until the first step
@@ -65,15 +77,18 @@ struct CtrlDesc {
   float Q[kMaxN], Qf[kMaxN];
   float shape[2 * kMaxShape];
   float g, inv_mass, arm_over_I;
-  double lambda, inv_lambda, mu_coarse, gamma_ctrl, gamma_bas;
+  double lambda, inv_lambda, mu_coarse, gamma_ctrl, gamma_bas, R_B_d;
   double umin_d[2], umax_d[2];
   int nscl;
   double sigma[4];
+  double Lsig[3];            // chol(Sigma): l00, l10, l11
+  double Sinv[4];            // gamma * Sigma^-1 (row-major; zero when gamma = 0)
   double x_goal[kMaxN];
   uint32_t key0, key1;
   double* U;                 // T x 2 nominal sequence
   float2* cU;                // T: U in FP32 for the next step
   float2* cA;                // T: gamma (S_e Sigma)^-1 u_t in FP32
+  float* cw;                 // T: R_B c_{t+1}, weight of step t's barrier sum
   DevState* st;
   const double* obst;        // J x 3 (cx, cy, r), padded to 16 bytes
   const double* x0;          // n (may be overridden per launch)
@@ -93,13 +108,14 @@ struct CtrlDesc {
 // barrier partials, reused as the raw obstacle staging buffer before the
 // rollout and as the nominal-rollout buffers in the final stage.
 struct SmemLayout {
-  int obs4, region, dU, pose, posB, Uf, Af, red, Us, colhi, collo, scl, xrf, shp, eS, total;
+  int obs4, region, dU, pose, posB, Uf, Af, red, Us, Usf, colhi, collo, scl, xrf, shp, eS, cw,
+      total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, int J, int n,
-                                                  int nscl) {
+                                                  int nscl, int nwarps) {
   SmemLayout L;
   int off = 0;
   L.obs4 = off;
@@ -108,13 +124,15 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, i
   L.region = off;
   int pose_b = 16 * TC * S;
   int dU_b = 8 * T * S;
-  int posB_b = 4 * TC * S * P;
-  int main_b = pose_b + dU_b + posB_b;
+  int uB_b = 8 * TC * S;
+  int main_b = pose_b + dU_b + uB_b;
   int raw_b = align_up(24 * J, 16);
-  int nom_b = 16 * T + 4 * T * P;
+  int nom_b = 16 * T + 8 * T;
+  int merge_b = 8 * 2 * T * nwarps;  // per-warp float-pair column sums of a merge
   int reg = main_b;
   if (raw_b > reg) reg = raw_b;
   if (nom_b > reg) reg = nom_b;
+  if (merge_b > reg) reg = merge_b;
   L.pose = off;
   L.dU = off + pose_b;
   L.posB = off + pose_b + dU_b;
@@ -123,6 +141,8 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, i
   off += 8 * 4 * 32;
   L.Us = off;
   off += 16 * T;
+  L.Usf = off;
+  off += 8 * T;
   L.Uf = off;
   off += 8 * T;
   L.Af = off;
@@ -140,6 +160,8 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, i
   off += 8 * kMaxShape;
   L.eS = off;
   off += 4 * 32;
+  L.cw = off;
+  off += 4 * T;
   L.total = align_up(off, 16);
   return L;
 }
@@ -299,50 +321,45 @@ struct Dyn<1> {  // planar quadrotor (y, z, phi, ydot, zdot, phidot), u = thrust
 // ------------------------------------------------------------ tile kernel body
 struct TileScratch {
   uint64_t mbar;
-  uint32_t mbar_phase;
   int flag;
-  float beta_d_f;
-  double beta0, beta_d, C0;
-  float L00, L10, L11;
-  float ox_f;  // unused padding
+  double beta0, beta_d, Kconst;
 };
 
-// Fused barrier over positions [0, npos) whose poses are pose[(tl*S+s)] and
-// shape points shp[p], position index = (tl*S + s)*P + p.  Writes the partial
-// sum per position with the sign bit set when some h <= 0.
+// Fused barrier over nunits (step, sample) units; unit u has pose pose[u]
+// and P shape points shp[0..P).  Each thread takes NPOS / P whole units at a
+// time (NPOS >= P), keeps their world points in registers and streams every
+// obstacle: h = |p - c|^2 - r^2 evaluated as fma(dx, dx, fma(dy, dy, -r^2)),
+// term 1 / max(h, h_eps) by the approximate reciprocal.  A unit's points are
+// summed exactly (TwoSum) into (hi, lo); the sign bit of hi marks a unit in
+// which some h <= 0 (collision).
 template <int NPOS>
-__device__ __forceinline__ void barrier_positions(int npos, int S, int P, int J,
-                                                  const float4* __restrict__ pose,
-                                                  const float2* __restrict__ shp,
-                                                  const float4* __restrict__ obs4, float h_eps,
-                                                  float* __restrict__ posB, int tid, int nthreads) {
-  const int SP = S * P;
-  for (int base = tid * NPOS; base < npos; base += nthreads * NPOS) {
+__device__ __forceinline__ void barrier_units(int nunits, int P, int J,
+                                              const float4* __restrict__ pose,
+                                              const float2* __restrict__ shp,
+                                              const float4* __restrict__ obs4, float h_eps,
+                                              float2* __restrict__ uB, int tid, int nthreads) {
+  const int upt = NPOS / P;  // units per thread per round
+  const int used = upt * P;
+  for (int ub = tid * upt; ub < nunits; ub += nthreads * upt) {
     float X[NPOS], Y[NPOS], acc[NPOS], mn[NPOS];
-    int idx = base;
-    int tl = idx / SP;
-    int r = idx - tl * SP;
-    int s = r / P;
-    int p = r - s * P;
+    int uu = 0, p = 0;
 #pragma unroll
     for (int i = 0; i < NPOS; ++i) {
-      int q = (base + i < npos) ? (tl * S + s) : 0;
-      float4 ps = pose[q];
-      float2 sh = shp[(base + i < npos) ? p : 0];
+      const int u = ub + uu;
+      const bool ok = (i < used) && (u < nunits);
+      const float4 ps = pose[ok ? u : ub];
+      const float2 sh = shp[ok ? p : 0];
       X[i] = fmaf(ps.z, sh.x, fmaf(-ps.w, sh.y, ps.x));
       Y[i] = fmaf(ps.w, sh.x, fmaf(ps.z, sh.y, ps.y));
       acc[i] = 0.0f;
       mn[i] = __int_as_float(0x7f800000);
       if (++p == P) {
         p = 0;
-        if (++s == S) {
-          s = 0;
-          ++tl;
-        }
+        ++uu;
       }
     }
     for (int j = 0; j < J; ++j) {
-      float4 o = obs4[j];
+      const float4 o = obs4[j];
 #pragma unroll
       for (int i = 0; i < NPOS; ++i) {
         float dx = X[i] - o.x;
@@ -352,41 +369,95 @@ __device__ __forceinline__ void barrier_positions(int npos, int S, int P, int J,
         acc[i] += rcp_approx(fmaxf(h, h_eps));
       }
     }
+    FF f = {0.0f, 0.0f};
+    bool coll = false;
+    uu = 0;
+    p = 0;
 #pragma unroll
-    for (int i = 0; i < NPOS; ++i)
-      if (base + i < npos) posB[base + i] = (mn[i] <= 0.0f) ? -acc[i] : acc[i];
+    for (int i = 0; i < NPOS; ++i) {
+      if (i < used) {
+        ff_add(f, acc[i]);
+        coll |= (mn[i] <= 0.0f);
+        if (++p == P) {
+          const int u = ub + uu;
+          if (u < nunits) uB[u] = make_float2(coll ? -f.hi : f.hi, f.lo);
+          f.hi = 0.0f;
+          f.lo = 0.0f;
+          coll = false;
+          p = 0;
+          ++uu;
+        }
+      }
+    }
   }
+}
+
+// Two float pairs added exactly up to the final rounding of the low part.
+__device__ __forceinline__ FF ff_sum(FF a, FF b) {
+  FF r = a;
+  ff_add(r, b.hi);
+  r.lo += b.lo;
+  return r;
 }
 
 // Merge n partial results (rho_i, Z_i, cols_i[ncol]) taken relative to their
 // own minima into one relative to the common minimum: the log-sum-exp merge
-// of Eq. 4's numerator and denominator.  All threads of the CTA call it.
+// of Eq. 4's numerator and denominator.  Warp w takes sources w, w + nwarps,
+// ...; lane l takes columns l, l + 32, ... (ncol <= 32 * kMaxColsPerLane), so
+// every load instruction reads a contiguous row segment and many rows are in
+// flight at once; the per-warp float-pair sums are then added in warp order.
+// All threads of the CTA call it.  buf: nwarps x ncol float pairs.
 // Outputs in shared memory: *rho_out, *Z_out, col_hi/col_lo[ncol].
+constexpr int kMaxColsPerLane = 16;  // 2 T <= 512
 __device__ inline void merge_partials(int n, const double2* rz, const float* cols, int ncol,
-                                      double lambda, float* scl, double* rho_out, double* Z_out,
-                                      float* col_hi, float* col_lo, double* red, int tid,
-                                      int nthreads) {
-  // global minimum: every thread scans (n is small)
-  double rho = __longlong_as_double(0x7ff0000000000000ll);
-  for (int i = 0; i < n; ++i) rho = fmin(rho, __ldcg(&rz[i].x));
-  // scale factors
-  for (int i = tid; i < n; i += nthreads) {
-    double2 v = __ldcg(&rz[i]);
-    scl[i] = (float)exp(-(v.x - rho) / lambda);
-  }
-  __syncthreads();
-  if (tid < 32) {
+                                      double inv_lambda, float* scl, double* rho_out,
+                                      double* Z_out, float* col_hi, float* col_lo, FF* buf,
+                                      double* red, int tid, int nthreads) {
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+  if (warp == 0) {
+    double r = __longlong_as_double(0x7ff0000000000000ll);
+    for (int i = lane; i < n; i += 32) r = fmin(r, __ldcg(&rz[i].x));
+    r = warp_min_d(r);
     double z = 0.0;
-    for (int i = tid; i < n; i += 32) z += __ldcg(&rz[i].y) * (double)scl[i];
+    for (int i = lane; i < n; i += 32) {
+      double2 v = __ldcg(&rz[i]);
+      float s = expf(-(float)((v.x - r) * inv_lambda));
+      scl[i] = s;
+      z += v.y * (double)s;
+    }
     z = warp_sum_d(z);
-    if (tid == 0) {
-      *rho_out = rho;
+    if (lane == 0) {
+      *rho_out = r;
       *Z_out = z;
     }
   }
+  __syncthreads();
+  FF acc[kMaxColsPerLane];
+#pragma unroll
+  for (int j = 0; j < kMaxColsPerLane; ++j) acc[j].hi = acc[j].lo = 0.0f;
+  const int nj = (ncol + 31) / 32;
+  for (int i = warp; i < n; i += nwarps) {
+    const float s = scl[i];
+    const float* row = cols + (size_t)i * ncol;
+    float v[kMaxColsPerLane];
+#pragma unroll
+    for (int j = 0; j < kMaxColsPerLane; ++j) {
+      int c = lane + 32 * j;
+      v[j] = (j < nj && c < ncol) ? __ldcg(row + c) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxColsPerLane; ++j)
+      if (j < nj) ff_add(acc[j], v[j] * s);
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxColsPerLane; ++j) {
+    int c = lane + 32 * j;
+    if (j < nj && c < ncol) buf[warp * ncol + c] = acc[j];
+  }
+  __syncthreads();
   for (int c = tid; c < ncol; c += nthreads) {
-    FF a = {0.0f, 0.0f};
-    for (int i = 0; i < n; ++i) ff_add(a, __ldcg(&cols[(size_t)i * ncol + c]) * scl[i]);
+    FF a = buf[c];
+    for (int w = 1; w < nwarps; ++w) a = ff_sum(a, buf[w * ncol + c]);
     col_hi[c] = a.hi;
     col_lo[c] = a.lo;
   }

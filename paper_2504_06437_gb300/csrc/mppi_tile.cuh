@@ -8,34 +8,58 @@ namespace dbm {
 
 constexpr int kTmaPolls = 1 << 22;
 
+// Obstacle staging: 1 = bulk TMA copy into shared memory (mbarrier
+// completion), 0 = coalesced loads by all threads.
+#ifndef DBM_STAGE_TMA
+#define DBM_STAGE_TMA 1
+#endif
+
+// TwoProd: c * b = ph + pe exactly, added to the float pair.
+__device__ __forceinline__ void ff_add_prod(FF& a, float c, float bh, float bl) {
+  float ph = c * bh;
+  float pe = fmaf(c, bh, -ph);
+  ff_add(a, ph);
+  a.lo += fmaf(c, bl, pe);
+}
+
+// Constants of the controller that never change: the unrolled DBaS weights
+// c_s (scaled by R_B) and their sums.  One CTA, at creation.
+__device__ inline void init_constants(const CtrlDesc& D, int tid, int nthreads) {
+  const int T = D.T;
+  const double g = D.gamma_bas;
+  for (int t = tid; t < T; t += nthreads) {
+    // step t produces x_{t+1}: c_{t+1} = (1 - g^(T - t)) / (1 - g)
+    double c = (1.0 - pow(g, (double)(T - t))) / (1.0 - g);
+    D.cw[t] = (float)(D.R_B_d * c);
+  }
+  if (tid == 0) {
+    double gT = pow(g, (double)T);
+    D.st->g1 = g * (1.0 - gT) / (1.0 - g);
+    D.st->csum = (T - D.st->g1) / (1.0 - g);
+  }
+}
+
 // Per-step constants that depend only on the controller state (U, S_e):
-// the Cholesky factor of S_e Sigma, a_t = gamma (S_e Sigma)^-1 u_t, u_t in
-// FP32, and C0 = sum_t u_t . a_t, the part of the control cost of Eq. 9
-// (Algorithm 1 form gamma u^T (S_e Sigma)^-1 v) that every sample shares.
-// Run by one CTA after each shift, and by a one-CTA kernel after the host
-// sets the state.  red: >= 40 doubles of shared memory.
+// chol(S_e Sigma) = sqrt(S_e) chol(Sigma), a_t = gamma (S_e Sigma)^-1 u_t
+// = (gamma Sigma^-1 / S_e) u_t, u_t in FP32, and C0 = sum_t u_t . a_t, the
+// part of the control cost of Eq. 9 (Algorithm 1 form
+// gamma u^T (S_e Sigma)^-1 v) that every sample shares.  Run by one CTA after
+// each shift, and by a one-CTA kernel after the host sets the state.
+// red: >= 32 doubles of shared memory.
 __device__ inline void prep_constants(const CtrlDesc& D, double* red, int tid, int nthreads) {
   DevState* st = D.st;
   const int T = D.T;
   __syncthreads();
+  const double Se = st->S_e;
+  const double inv_Se = 1.0 / Se;
   if (tid == 0) {
-    double Se = st->S_e;
-    double a = Se * D.sigma[0], b = Se * D.sigma[1], c = Se * D.sigma[2], d = Se * D.sigma[3];
-    double l00 = sqrt(fmax(a, 0.0));
-    double l10 = l00 > 0.0 ? c / l00 : 0.0;
-    double l11 = sqrt(fmax(d - l10 * l10, 0.0));
-    st->L00 = (float)l00;
-    st->L10 = (float)l10;
-    st->L11 = (float)l11;
-    double det = a * d - b * c;
-    double gi = D.gamma_ctrl != 0.0 ? D.gamma_ctrl / det : 0.0;
-    red[32] = gi * d;
-    red[33] = -gi * b;
-    red[34] = -gi * c;
-    red[35] = gi * a;
+    const double r = sqrt(Se);
+    st->L00 = (float)(r * D.Lsig[0]);
+    st->L10 = (float)(r * D.Lsig[1]);
+    st->L11 = (float)(r * D.Lsig[2]);
   }
-  __syncthreads();
-  const double M00 = red[32], M01 = red[33], M10 = red[34], M11 = red[35];
+  const double M00 = D.Sinv[0] * inv_Se, M01 = D.Sinv[1] * inv_Se;
+  const double M10 = D.Sinv[2] * inv_Se, M11 = D.Sinv[3] * inv_Se;
   double c0 = 0.0;
   for (int t = tid; t < T; t += nthreads) {
     double u0 = D.U[2 * t], u1 = D.U[2 * t + 1];
@@ -55,6 +79,26 @@ __device__ inline void prep_constants(const CtrlDesc& D, double* red, int tid, i
   __syncthreads();
 }
 
+// Barrier-state cost of one trajectory from its unit sums uB[0..T): the
+// sample-dependent part sum_s R_B c_s b_s, spread over the lanes of one warp
+// (all lanes call it), plus the FP64 constant.
+__device__ __forceinline__ double dbas_cost_warp(const float2* uB, const float* cw, int T,
+                                                 double Kconst, int lane) {
+  FF a = {0.0f, 0.0f};
+  for (int t = lane; t < T; t += 32) {
+    float2 v = uB[t];
+    ff_add_prod(a, cw[t], fabsf(v.x), v.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a = ff_sum(a, b);
+  }
+  return (double)a.hi + (double)a.lo + Kconst;
+}
+
 // Final stage (one CTA per controller per step): U* from the merged sums
 // (Eq. 4), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"),
 // S_e (Eq. 10, C_B floored at 0 inside the logarithm), shift, state update.
@@ -65,12 +109,14 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int T = D.T, P = D.P;
   double* Us = reinterpret_cast<double*>(smem + L.Us);
+  float2* Usf = reinterpret_cast<float2*>(smem + L.Usf);
   const float* col_hi = reinterpret_cast<const float*>(smem + L.colhi);
   const float* col_lo = reinterpret_cast<const float*>(smem + L.collo);
   float4* pose_nom = reinterpret_cast<float4*>(smem + L.region);
-  float* posB_nom = reinterpret_cast<float*>(smem + L.region + 16 * T);
+  float2* uB_nom = reinterpret_cast<float2*>(smem + L.region + 16 * T);
   const float2* shp = reinterpret_cast<const float2*>(smem + L.shp);
   const float4* obs4 = reinterpret_cast<const float4*>(smem + L.obs4);
+  const float* cw = reinterpret_cast<const float*>(smem + L.cw);
   const double invZ = 1.0 / Z;
   for (int c = tid; c < 2 * T; c += nthreads) {
     int d = c & 1;
@@ -78,6 +124,7 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
     double u = D.U[c] + du;
     u = fmin(fmax(u, D.umin_d[d]), D.umax_d[d]);
     Us[c] = u;
+    reinterpret_cast<float*>(Usf)[c] = (float)u;
     D.Ustar[c] = u;
   }
   __syncthreads();
@@ -90,38 +137,35 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
     float sn, cs;
     sincosf(x[2], &sn, &cs);
     for (int t = 0; t < T; ++t) {
-      Dyn<MODEL>::step(x, cs, sn, (float)Us[2 * t], (float)Us[2 * t + 1], D);
+      const float2 u = Usf[t];
+      Dyn<MODEL>::step(x, cs, sn, u.x, u.y, D);
       pose_nom[t] = make_float4(x[0], x[1], cs, sn);
     }
   }
   __syncthreads();
-  barrier_positions<NPOS>(T * P, 1, P, D.J, pose_nom, shp, obs4, D.h_eps, posB_nom, tid, nthreads);
+  barrier_units<NPOS>(T, P, D.J, pose_nom, shp, obs4, D.h_eps, uB_nom, tid, nthreads);
   __syncthreads();
-  if (tid == 0) {
-    float w = (float)ts.beta0;
-    FF cb = {0.0f, 0.0f};
-    for (int t = 0; t < T; ++t) {
-      float b = 0.0f;
-      for (int p = 0; p < P; ++p) b += fabsf(posB_nom[t * P + p]);
-      w = fmaf(D.gamma_bas_f, w - ts.beta_d_f, b);
-      ff_add(cb, D.R_B * w);
+  if (tid < 32) {
+    const double CB = dbas_cost_warp(uB_nom, cw, T, ts.Kconst, tid);
+    if (tid == 0) {
+      DevState* st = D.st;
+      const double S_e_used = st->S_e;
+      // Eq. 10, C_B floored at 0 inside the logarithm
+      const float arg = (float)(2.718281828459045 + fmax(CB, 0.0));
+      const double S_e_next = D.mu_coarse > 0.0 ? D.mu_coarse * (double)logf(arg) : 1.0;
+      st->rho = rho;
+      st->Z = Z;
+      st->CB_star = CB;
+      st->beta_used = ts.beta0;
+      st->beta_d = ts.beta_d;
+      st->S_e_used = S_e_used;
+      st->u0[0] = Us[0];
+      st->u0[1] = Us[1];
+      st->S_e = S_e_next;
+      st->beta = ts.beta0;
+      st->first = 0;
+      st->iter = st->iter + 1ull;
     }
-    double CB = (double)cb.hi + (double)cb.lo;
-    DevState* st = D.st;
-    double S_e_used = st->S_e;
-    double S_e_next = D.mu_coarse > 0.0 ? D.mu_coarse * log(2.718281828459045 + fmax(CB, 0.0)) : 1.0;
-    st->rho = rho;
-    st->Z = Z;
-    st->CB_star = CB;
-    st->beta_used = ts.beta0;
-    st->beta_d = ts.beta_d;
-    st->S_e_used = S_e_used;
-    st->u0[0] = Us[0];
-    st->u0[1] = Us[1];
-    st->S_e = S_e_next;
-    st->beta = ts.beta0;
-    st->first = 0;
-    st->iter = st->iter + 1ull;
   }
   // shift (Algorithm 1, last loop): u_{t-1} <- u*_t, the last entry kept
   for (int c = tid; c < 2 * T; c += nthreads) {
@@ -132,38 +176,43 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
   prep_constants(D, reinterpret_cast<double*>(smem + L.red), tid, nthreads);
 }
 
-// One tile of one controller.  ts.mbar must be initialised; ts.mbar_phase is
-// the parity of its next completion.
+// One tile of one controller.  ts.mbar must be initialised; mbar_phase is
+// each thread's own copy of the parity of the barrier's next completion.
 template <int MODEL, int NPOS>
 __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
-                         const double* __restrict__ xrefg, char* smem, TileScratch& ts) {
+                         const double* __restrict__ xrefg, char* smem, TileScratch& ts,
+                         uint32_t& mbar_phase) {
   constexpr int n = Dyn<MODEL>::n;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   const int T = D.T, S = D.S, P = D.P, J = D.J, TC = D.TC, K = D.K;
-  const SmemLayout L = smem_layout(T, S, TC, P, J, n, D.nscl);
+  const SmemLayout L = smem_layout(T, S, TC, P, J, n, D.nscl, nwarps);
   float4* obs4 = reinterpret_cast<float4*>(smem + L.obs4);
   float4* pose = reinterpret_cast<float4*>(smem + L.pose);
   float2* dU = reinterpret_cast<float2*>(smem + L.dU);
-  float* posB = reinterpret_cast<float*>(smem + L.posB);
+  float2* uB = reinterpret_cast<float2*>(smem + L.posB);
   float2* Uf = reinterpret_cast<float2*>(smem + L.Uf);
   float2* Af = reinterpret_cast<float2*>(smem + L.Af);
   float* xrf = reinterpret_cast<float*>(smem + L.xrf);
   float2* shp = reinterpret_cast<float2*>(smem + L.shp);
   float* eS = reinterpret_cast<float*>(smem + L.eS);
+  float* cw = reinterpret_cast<float*>(smem + L.cw);
   double* red = reinterpret_cast<double*>(smem + L.red);
   DevState* st = D.st;
   const int k0 = tile * S;
 
   // ---- prologue: stage obstacles (TMA bulk copy), per-step constants
   __syncthreads();  // previous use of shared memory by this CTA is over
+#if DBM_STAGE_TMA
   if (tid == 0 && J > 0)
     tma_bulk_g2s(smem + L.region, D.obst, (uint32_t)align_up(24 * J, 16), &ts.mbar);
+#endif
   if (tid < P) shp[tid] = make_float2(D.shape[2 * tid], D.shape[2 * tid + 1]);
   const double ox = x0g[0], oy = x0g[1];
   for (int t = tid; t < T; t += nthreads) {
     Uf[t] = D.cU[t];
     Af[t] = D.cA[t];
+    cw[t] = D.cw[t];
   }
   for (int i = tid; i < (T + 1) * n; i += nthreads) {
     int d = i % n;
@@ -173,13 +222,17 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
     xrf[i] = (float)v;
   }
   if (J > 0) {
-    bool ok = mbar_wait(&ts.mbar, ts.mbar_phase, kTmaPolls);
+#if DBM_STAGE_TMA
+    bool ok = mbar_wait(&ts.mbar, mbar_phase, kTmaPolls);
     if (!ok) {
       if (tid == 0) atomicExch(&st->status, kStatusTimeout);
-      mbar_wait(&ts.mbar, ts.mbar_phase, kTmaPolls);
+      mbar_wait(&ts.mbar, mbar_phase, kTmaPolls);
     }
-    ts.mbar_phase ^= 1u;
+    mbar_phase ^= 1u;  // every thread flips its own copy
     const double* raw = reinterpret_cast<const double*>(smem + L.region);
+#else
+    const double* raw = D.obst;
+#endif
     // the raw (region) and converted (obs4) areas are distinct
     for (int j = tid; j < J; j += nthreads) {
       double cx = raw[3 * j], cy = raw[3 * j + 1], r = raw[3 * j + 2];
@@ -235,16 +288,17 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
       sbd += red[2 * w];
       sb0 += red[2 * w + 1];
     }
+    double beta0 = st->first ? sb0 : sb0 + D.gamma_bas * (st->beta - sbd);
     ts.beta_d = sbd;
-    ts.beta_d_f = (float)sbd;
-    ts.C0 = st->C0;
-    ts.beta0 = st->first ? sb0 : sb0 + D.gamma_bas * (st->beta - sbd);
+    ts.beta0 = beta0;
+    // sample-independent part of sum_t R_B w_t (unrolled Eq. 7)
+    ts.Kconst = D.R_B_d * (beta0 * st->g1 - D.gamma_bas * sbd * st->csum);
   }
   __syncthreads();
 
   // ---- rollout over chunks
   float x[n];
-  float cs = 1.0f, sn = 0.0f, w = 0.0f;
+  float cs = 1.0f, sn = 0.0f;
   FF acc1 = {0.0f, 0.0f}, acc2 = {0.0f, 0.0f};
   bool coll = false;
   if (warp == 0) {
@@ -253,23 +307,15 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
 #pragma unroll
     for (int d = 2; d < n; ++d) x[d] = (float)x0g[d];
     sincosf(x[2], &sn, &cs);
-    w = (float)ts.beta0;
   }
-  const float gb = D.gamma_bas_f, bdf = ts.beta_d_f;
+  // barrier-state and collision costs of chunk c from its unit sums
   auto recur_chunk = [&](int c) {
     int t0 = c * TC;
     int TCc = min(TC, T - t0);
     for (int tl = 0; tl < TCc; ++tl) {
-      float b = 0.0f;
-      bool cl = false;
-      const float* pb = posB + (tl * S + lane) * P;
-      for (int p = 0; p < P; ++p) {
-        float v = pb[p];
-        cl |= (__float_as_int(v) < 0);
-        b += fabsf(v);
-      }
-      w = fmaf(gb, w - bdf, b);
-      ff_add(acc2, D.R_B * w);
+      float2 v = uB[tl * S + lane];
+      bool cl = __float_as_int(v.x) < 0;
+      ff_add_prod(acc2, cw[t0 + tl], fabsf(v.x), v.y);
       if (cl) ff_add(acc2, D.C_coll);
       coll |= cl;
     }
@@ -307,7 +353,7 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
       draw_chunk(c + 1, 32, nthreads - 32);
     }
     __syncthreads();
-    barrier_positions<NPOS>(TCc * S * P, S, P, J, pose, shp, obs4, D.h_eps, posB, tid, nthreads);
+    barrier_units<NPOS>(TCc * S, P, J, pose, shp, obs4, D.h_eps, uB, tid, nthreads);
     __syncthreads();
   }
 
@@ -326,7 +372,7 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
       }
       double s = (double)acc1.hi + (double)acc2.hi;
       s += (double)acc1.lo + (double)acc2.lo;
-      s += ts.C0 + (double)phi;
+      s += st->C0 + ts.Kconst + (double)phi;
       if (valid) Sk = s;
     }
     double rho_c = warp_min_d(Sk);
@@ -337,7 +383,10 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
       D.costs[k0 + lane] = Sk;
       D.coll[k0 + lane] = coll ? 1 : 0;
     }
-    if (lane == 0) D.part_rz[tile] = make_double2(rho_c, Zc);
+    if (lane == 0) {
+      D.part_rz[tile] = make_double2(rho_c, Zc);
+      __threadfence();
+    }
   }
   __syncthreads();
   {
@@ -349,10 +398,10 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
       float b = warp_sum_f(e * du.y);
       if (lane == 0) reinterpret_cast<float2*>(prow)[t] = make_float2(a, b);
     }
+    if (lane == 0) __threadfence();  // the writers of the tile's partials
   }
 
-  // ---- two-level last-arriver merge: every writer fences, then one ticket
-  __threadfence();
+  // ---- two-level last-arriver merge: the writers fenced, then one ticket
   __syncthreads();
   const int g = tile / D.GT;
   const int m0 = g * D.GT;
@@ -367,16 +416,22 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
   float* scl = reinterpret_cast<float*>(smem + L.scl);
   float* col_hi = reinterpret_cast<float*>(smem + L.colhi);
   float* col_lo = reinterpret_cast<float*>(smem + L.collo);
+  FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
   double* mres = red + 100;
   const int ncol = 2 * T;
-  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.lambda, scl, mres,
-                 mres + 1, col_hi, col_lo, red, tid, nthreads);
-  for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
+  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.inv_lambda, scl,
+                 mres, mres + 1, col_hi, col_lo, mbuf, red, tid, nthreads);
+  bool wrote = false;
+  for (int c = tid; c < ncol; c += nthreads) {
+    D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
+    wrote = true;
+  }
   if (tid == 0) {
     D.gpart_rz[g] = make_double2(mres[0], mres[1]);
     D.counters[g] = 0u;
+    wrote = true;
   }
-  __threadfence();
+  if (wrote) __threadfence();
   __syncthreads();
   if (tid == 0) {
     unsigned tk = atomicAdd(&D.counters[D.nGroups], 1u);
@@ -385,8 +440,8 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
   __syncthreads();
   if (!ts.flag) return;
   __threadfence();
-  merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.lambda, scl, mres, mres + 1, col_hi,
-                 col_lo, red, tid, nthreads);
+  merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda, scl, mres, mres + 1, col_hi,
+                 col_lo, mbuf, red, tid, nthreads);
   if (tid == 0) D.counters[D.nGroups] = 0u;
   final_stage<MODEL, NPOS>(D, smem, L, ts, mres[0], mres[1], x0g);
 }
