@@ -167,6 +167,33 @@ int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta,
 int mppi_debug_draws(const mppi_params* p, double S_e, uint64_t iter, int32_t K,
                      int32_t T, uint32_t* raw, float* du);
 
+/* One step without any device allocation and without a context, for callers
+ * that may not allocate once they run: real-time control loops that keep
+ * every step's latency bounded (cudaMalloc can block and synchronise the
+ * device) and programs whose device memory belongs to another allocator.
+ * The paper has no counterpart; it is the step of mppi_step_device() with its
+ * scratch in a fixed 8 MiB array inside the library (each GPU that loads the
+ * library keeps it until the process exits).
+ *   d_obst   device, J x 3 (cx, cy, r); copied into the scratch.
+ *   d_x0     device, n doubles;  d_xref device, (T+1) x n.
+ *   d_U      device, T x 2, in/out: the nominal sequence; shifted on return.
+ *   d_ctl    device, 5 doubles, in/out: {S_e, beta, first (1 before the
+ *            first step, else 0), iteration count, status}; start a
+ *            controller with {mu (or 1 if mu <= 0), 0, 1, 0, 0}.  status
+ *            becomes 1 if a bounded device wait expired.
+ *   d_u0     device out, 2 doubles: u*_0.
+ *   d_costs  device out, K doubles, or NULL.
+ * All work is enqueued on `stream` (NULL = the legacy default stream); the
+ * call returns without waiting.  The first call on each device looks up the
+ * array's device address and sets kernel attributes, so make it before any
+ * stream capture.  Every call shares the one array: calls whose GPU work
+ * overlaps (other streams, other host threads) race; order them.  Errors:
+ * MPPI_EINVAL (bad params, NULL pointer, or a problem whose scratch exceeds
+ * the 8 MiB limit -- the message gives the bytes needed), MPPI_ECUDA. */
+int mppi_step_static(const mppi_params* p, const double* d_obst, int32_t J,
+                     const double* d_x0, const double* d_xref, double* d_U,
+                     double* d_ctl, double* d_u0, double* d_costs, void* stream);
+
 /* Release everything owned by the context.  NULL is a no-op. */
 int mppi_destroy(mppi_ctx* c);
 

@@ -681,3 +681,140 @@ int mppi_destroy(mppi_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free step.  For callers that may not allocate device memory once
+// they run: real-time control loops that must keep every step's latency
+// bounded (cudaMalloc can block and synchronise the device), and host
+// programs whose device memory is owned by another allocator.  Everything
+// the step needs beyond its inputs and outputs lives in this fixed array,
+// which every GPU that loads the library keeps until the process exits.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 8u << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+unsigned char* g_static_base[kMaxStaticDevices] = {nullptr};  // device address, per device
+
+// Device-side copy of the caller's controller state into the scratch state
+// block, ticket counters cleared, constants derived; the caller's ctl is
+// {S_e, beta, first, iter, status}.
+__global__ void static_prologue(const __grid_constant__ CtrlDesc D, const double* __restrict__ ctl,
+                                int n_counters) {
+  __shared__ double red[64];
+  if (threadIdx.x == 0) {
+    D.st->S_e = ctl[0];
+    D.st->beta = ctl[1];
+    D.st->first = ctl[2] != 0.0 ? 1 : 0;
+    D.st->iter = (unsigned long long)ctl[3];
+    D.st->status = 0;
+  }
+  for (int i = threadIdx.x; i < n_counters; i += blockDim.x) D.counters[i] = 0u;
+  __syncthreads();
+  init_constants(D, threadIdx.x, blockDim.x);
+  prep_constants(D, red, threadIdx.x, blockDim.x);
+}
+
+__global__ void static_epilogue(const DevState* __restrict__ st, double* __restrict__ ctl,
+                                double* __restrict__ u0) {
+  if (threadIdx.x == 0) {
+    ctl[0] = st->S_e;
+    ctl[1] = st->beta;
+    ctl[2] = st->first;
+    ctl[3] = (double)st->iter;
+    ctl[4] = st->status;
+    u0[0] = st->u0[0];
+    u0[1] = st->u0[1];
+  }
+}
+
+size_t carve(size_t* off, size_t bytes) {
+  size_t at = *off;
+  *off += (bytes + 255) & ~(size_t)255;
+  return at;
+}
+
+}  // namespace
+
+extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int32_t J,
+                                const double* d_x0, const double* d_xref, double* d_U,
+                                double* d_ctl, double* d_u0, double* d_costs, void* stream) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (J < 0 || J > MPPI_MAX_OBSTACLES)
+    return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
+  if ((J > 0 && !d_obst) || !d_x0 || !d_xref || !d_U || !d_ctl || !d_u0)
+    return fail(MPPI_EINVAL, "a required device pointer is NULL");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxStaticDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
+  if (!g_static_base[dev]) {
+    // set-up, once per device, with that device current
+    void* base = nullptr;
+    CK(cudaGetSymbolAddress(&base, g_static_scratch));
+    const int lim = max_smem_optin();
+    const StepFn fns[6] = {step_kernel<0, 8>, step_kernel<0, 14>, step_kernel<0, 16>,
+                           step_kernel<1, 8>, step_kernel<1, 14>, step_kernel<1, 16>};
+    for (StepFn f : fns) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    g_static_base[dev] = (unsigned char*)base;
+  }
+  unsigned char* base = g_static_base[dev];
+  mppi_ctx c;  // on the stack: only its descriptor logic is used
+  c.p = *p;
+  c.n = state_dim(p->model);
+  rc = choose_tiling(p, nullptr, J, &c.tl, &c.smem);
+  if (rc) return rc;
+  const int T = p->T, K = p->K;
+  const int nTiles = (K + c.tl.samples_per_cta - 1) / c.tl.samples_per_cta;
+  int GT = (nTiles + 63) / 64;
+  if (GT < 32) GT = 32;
+  const int nGroups = (nTiles + GT - 1) / GT;
+  size_t off = 0;
+  const size_t o_st = carve(&off, sizeof(DevState));
+  const size_t o_cU = carve(&off, sizeof(float2) * T);
+  const size_t o_cA = carve(&off, sizeof(float2) * T);
+  const size_t o_cw = carve(&off, sizeof(float) * T);
+  const size_t o_obst = carve(&off, (size_t)align_up(24 * (J > 0 ? J : 1), 16));
+  const size_t o_part = carve(&off, sizeof(float) * (size_t)nTiles * 2 * T);
+  const size_t o_prz = carve(&off, sizeof(double2) * nTiles);
+  const size_t o_gpart = carve(&off, sizeof(float) * (size_t)nGroups * 2 * T);
+  const size_t o_grz = carve(&off, sizeof(double2) * nGroups);
+  const size_t o_cnt = carve(&off, sizeof(unsigned) * (nGroups + 1));
+  const size_t o_costs = d_costs ? 0 : carve(&off, sizeof(double) * K);
+  const size_t o_coll = carve(&off, (size_t)K);
+  const size_t o_Ustar = carve(&off, sizeof(double) * 2 * T);
+  if (off > kStaticScratchBytes)
+    return fail(MPPI_EINVAL, "step needs %zu bytes of static scratch, the limit is %zu", off,
+                kStaticScratchBytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  c.d_U = d_U;
+  c.d_cU = (float2*)(base + o_cU);
+  c.d_cA = (float2*)(base + o_cA);
+  c.d_cw = (float*)(base + o_cw);
+  c.d_st = (DevState*)(base + o_st);
+  c.d_obst = (double*)(base + o_obst);
+  c.d_in = nullptr;
+  c.d_part = (float*)(base + o_part);
+  c.d_part_rz = (double2*)(base + o_prz);
+  c.d_gpart = (float*)(base + o_gpart);
+  c.d_gpart_rz = (double2*)(base + o_grz);
+  c.d_cnt = (unsigned*)(base + o_cnt);
+  c.d_costs = d_costs ? d_costs : (double*)(base + o_costs);
+  c.d_coll = (uint8_t*)(base + o_coll);
+  c.d_Ustar = (double*)(base + o_Ustar);
+  fill_desc(&c);
+  c.D.J = J;
+  c.D.TC = c.tl.chunk_steps;
+  if (J > 0)
+    CK(cudaMemcpyAsync(c.d_obst, d_obst, sizeof(double) * 3 * J, cudaMemcpyDeviceToDevice, s));
+  static_prologue<<<1, 256, 0, s>>>(c.D, d_ctl, nGroups + 1);
+  CK(cudaGetLastError());
+  StepFn fn = pick_kernel(p->model, c.tl.positions_per_thread);
+  fn<<<c.D.nTiles, c.tl.threads, c.smem, s>>>(c.D, d_x0, d_xref);
+  CK(cudaGetLastError());
+  static_epilogue<<<1, 32, 0, s>>>(c.d_st, d_ctl, d_u0);
+  CK(cudaGetLastError());
+  return MPPI_OK;
+}
