@@ -230,6 +230,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-samples", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's default launch shape instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -248,7 +250,10 @@ def main():
     K, T, n = int(p["K"]), int(p["T"]), world.n
     P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
     J = int(world.obstacles.shape[0])
-    ctl = binding.Controller(p)
+    tiling, tune_us = None, None
+    if not args.no_autotune:
+        tiling, tune_us = binding.autotune(p, world.obstacles, iters=10)
+    ctl = binding.Controller(p, tiling=tiling)
     ctl.set_obstacles(world.obstacles)
     x0 = world.x_start
     xref = world.reference(x0)
@@ -321,7 +326,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(describe(world), parallelism=f"replicas x{ws}", tiling=tiling),
+            "config": dict(describe(world), parallelism=f"replicas x{ws}", tiling=tiling,
+                           tiling_source="autotuned" if tune_us else "default"),
             "latency_ms": {"p50": float(np.percentile(times_ms, 50)),
                            "p99": float(np.percentile(times_ms, 99))},
             "e2e": {"value": ws * K * T / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,

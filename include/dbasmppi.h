@@ -146,6 +146,16 @@ int mppi_get_debug(mppi_ctx* c, double* costs, uint8_t* collided,
  * mppi_get_control(c, u0, NULL) copies device -> host. */
 int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h);
 
+/* Autotuner: runs the step of this problem (params, obstacle set) under
+ * each candidate launch shape -- samples per CTA, threads per CTA, world
+ * points per barrier thread -- on scratch controllers, `iters` timed steps
+ * each (CUDA events), and returns the fastest in *best and its time per step
+ * in microseconds in *best_us (may be NULL).  Allocates and frees its own
+ * scratch controllers; synchronises.  Errors: MPPI_EINVAL, MPPI_ECUDA (no
+ * candidate ran). */
+int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J,
+                  int32_t iters, mppi_tiling* best, float* best_us);
+
 /* The launch shape in use and the number of CTAs of one step. */
 int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas);
 

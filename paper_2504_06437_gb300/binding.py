@@ -108,6 +108,8 @@ def load():
     lib.mppi_destroy.argtypes = [vp]
     lib.mppi_debug_draws.argtypes = [C.POINTER(Params), C.c_double, C.c_uint64, C.c_int32,
                                      C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
+    lib.mppi_autotune.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.c_int32,
+                                  C.POINTER(Tiling), C.POINTER(C.c_float)]
     lib.mppi_last_error.restype = C.c_char_p
     _lib = lib
     return lib
@@ -162,6 +164,18 @@ def debug_draws(cfg: dict, S_e: float, it: int, K: int, T: int):
                                    raw.ctypes.data_as(C.POINTER(C.c_uint32)),
                                    du.ctypes.data_as(C.POINTER(C.c_float))))
     return raw, du
+
+
+def autotune(cfg: dict, obstacles, iters: int = 10):
+    """Fastest launch shape for this problem: (tiling dict, microseconds per step)."""
+    p = make_params(cfg)
+    ob = _f64(obstacles).reshape(-1, 3)
+    t = Tiling()
+    us = C.c_float()
+    _check(load().mppi_autotune(C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0], int(iters),
+                                C.byref(t), C.byref(us)))
+    return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
+                positions_per_thread=t.positions_per_thread, chunk_steps=0), float(us.value)
 
 
 class Controller:

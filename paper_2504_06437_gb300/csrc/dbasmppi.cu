@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ CtrlD
 __global__ void prep_kernel(const __grid_constant__ CtrlDesc D, int init) {
   __shared__ double red[64];
   if (init) init_constants(D, threadIdx.x, blockDim.x);
-  prep_constants(D, red, threadIdx.x, blockDim.x);
+  prep_constants(D, D.U, red, threadIdx.x, blockDim.x);
 }
 
 __global__ void weights_kernel(const double* __restrict__ costs, int K,
@@ -190,9 +190,9 @@ struct mppi_ctx {
   double* d_obst = nullptr;
   double* d_in = nullptr;  // x0 (n) then xref ((T+1) n)
   float* d_part = nullptr;
-  double2* d_part_rz = nullptr;
+  float4* d_part_rz = nullptr;
   float* d_gpart = nullptr;
-  double2* d_gpart_rz = nullptr;
+  float4* d_gpart_rz = nullptr;
   unsigned* d_cnt = nullptr;
   double* d_costs = nullptr;
   uint8_t* d_coll = nullptr;
@@ -238,15 +238,16 @@ void free_ctx(mppi_ctx* c) {
 }
 
 // Launch shape: S samples per CTA, chosen so the grid covers the SMs at
-// least twice when K allows; TC steps per chunk so one chunk holds about
-// threads x NPOS barrier positions; shrink until shared memory fits.
+// least twice when K allows, then shrunk until the tile's shared memory
+// (whole-horizon poses and controls, obstacles) fits.
 int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tiling* out,
                   int* smem_out) {
   const int sms = num_sms();
   const int n = state_dim(p->model);
   mppi_tiling t = {0, 0, 0, 0};
   if (req) t = *req;
-  if (t.samples_per_cta <= 0) {
+  const bool fixed_S = t.samples_per_cta > 0;
+  if (!fixed_S) {
     long want = ((long)p->K + 2L * sms - 1) / (2L * sms);
     t.samples_per_cta = (int)(want < 1 ? 1 : (want > 32 ? 32 : want));
   }
@@ -259,30 +260,24 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
     return fail(MPPI_EINVAL, "positions_per_thread must be 8, 14 or 16");
   if (t.positions_per_thread < p->n_shape)
     return fail(MPPI_EINVAL, "positions_per_thread must be >= n_shape");
-  if (t.chunk_steps <= 0) {
-    // one round of barrier units per chunk: threads x (NPOS / P) units
-    int units = t.threads * (t.positions_per_thread / p->n_shape);
-    int tc = (units + t.samples_per_cta - 1) / t.samples_per_cta;
-    t.chunk_steps = tc < 1 ? 1 : tc;
-  }
-  if (t.chunk_steps > p->T) t.chunk_steps = p->T;
+  t.chunk_steps = 0;
   const int limit = max_smem_optin();
-  const int nTiles = (p->K + t.samples_per_cta - 1) / t.samples_per_cta;
-  int GT = (nTiles + 63) / 64;
-  if (GT < 32) GT = 32;
-  const int nGroups = (nTiles + GT - 1) / GT;
-  const int nscl = GT > nGroups ? GT : nGroups;
   for (;;) {
-    SmemLayout L =
-        smem_layout(p->T, t.samples_per_cta, t.chunk_steps, p->n_shape, J, n, nscl, t.threads / 32);
+    const int nTiles = (p->K + t.samples_per_cta - 1) / t.samples_per_cta;
+    int GT = (nTiles + 63) / 64;
+    if (GT < 32) GT = 32;
+    const int nGroups = (nTiles + GT - 1) / GT;
+    const int nscl = GT > nGroups ? GT : nGroups;
+    SmemLayout L = smem_layout(p->T, t.samples_per_cta, p->n_shape, J, n, nscl, t.threads / 32);
     if (L.total <= limit) {
       *smem_out = L.total;
       break;
     }
-    if (t.chunk_steps > 1) {
-      t.chunk_steps = (t.chunk_steps + 1) / 2;
+    if (t.samples_per_cta > 1 && !fixed_S) {
+      t.samples_per_cta = (t.samples_per_cta + 1) / 2;
     } else {
-      return fail(MPPI_EINVAL, "problem needs %d bytes of shared memory (limit %d)", L.total, limit);
+      return fail(MPPI_EINVAL, "problem needs %d bytes of shared memory per CTA (limit %d)",
+                  L.total, limit);
     }
   }
   *out = t;
@@ -301,7 +296,6 @@ void fill_desc(mppi_ctx* c) {
   D.P = p->n_shape;
   D.n = c->n;
   D.S = c->tl.samples_per_cta;
-  D.TC = c->tl.chunk_steps;
   D.NPOS = c->tl.positions_per_thread;
   D.nTiles = (p->K + D.S - 1) / D.S;
   D.GT = (D.nTiles + 63) / 64;
@@ -333,6 +327,7 @@ void fill_desc(mppi_ctx* c) {
   D.arm_over_I = p->model == MPPI_QUAD2D ? (float)(p->arm / p->inertia) : 0.0f;
   D.lambda = p->lambda;
   D.inv_lambda = 1.0 / p->lambda;
+  D.inv_lambda_f = (float)(1.0 / p->lambda);
   D.mu_coarse = p->mu_coarse;
   D.gamma_ctrl = p->gamma_ctrl;
   D.gamma_bas = p->gamma_bas;
@@ -425,9 +420,9 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   c->Jcap = 0;
   ALLOC(c->d_in, sizeof(double) * (n + (T + 1) * n));
   ALLOC(c->d_part, sizeof(float) * (size_t)nTiles * 2 * T);
-  ALLOC(c->d_part_rz, sizeof(double2) * nTiles);
+  ALLOC(c->d_part_rz, sizeof(float4) * nTiles);
   ALLOC(c->d_gpart, sizeof(float) * (size_t)nGroups * 2 * T);
-  ALLOC(c->d_gpart_rz, sizeof(double2) * nGroups);
+  ALLOC(c->d_gpart_rz, sizeof(float4) * nGroups);
   ALLOC(c->d_cnt, sizeof(unsigned) * (nGroups + 1));
   ALLOC(c->d_costs, sizeof(double) * K);
   ALLOC(c->d_coll, K);
@@ -509,9 +504,10 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
     CK(cudaMemset(c->d_obst, 0, bytes));
     CK(cudaMemcpy(c->d_obst, cxcyr, sizeof(double) * 3 * J, cudaMemcpyHostToDevice));
   }
+  if (t.samples_per_cta != c->tl.samples_per_cta)
+    return fail(MPPI_EINVAL, "obstacle set too large for the controller's tile shape");
   c->tl = t;
   c->smem = smem;
-  c->D.TC = t.chunk_steps;
   c->D.J = J;
   c->D.obst = c->d_obst;
   return MPPI_OK;
@@ -714,7 +710,7 @@ __global__ void static_prologue(const __grid_constant__ CtrlDesc D, const double
   for (int i = threadIdx.x; i < n_counters; i += blockDim.x) D.counters[i] = 0u;
   __syncthreads();
   init_constants(D, threadIdx.x, blockDim.x);
-  prep_constants(D, red, threadIdx.x, blockDim.x);
+  prep_constants(D, D.U, red, threadIdx.x, blockDim.x);
 }
 
 __global__ void static_epilogue(const DevState* __restrict__ st, double* __restrict__ ctl,
@@ -778,9 +774,9 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   const size_t o_cw = carve(&off, sizeof(float) * T);
   const size_t o_obst = carve(&off, (size_t)align_up(24 * (J > 0 ? J : 1), 16));
   const size_t o_part = carve(&off, sizeof(float) * (size_t)nTiles * 2 * T);
-  const size_t o_prz = carve(&off, sizeof(double2) * nTiles);
+  const size_t o_prz = carve(&off, sizeof(float4) * nTiles);
   const size_t o_gpart = carve(&off, sizeof(float) * (size_t)nGroups * 2 * T);
-  const size_t o_grz = carve(&off, sizeof(double2) * nGroups);
+  const size_t o_grz = carve(&off, sizeof(float4) * nGroups);
   const size_t o_cnt = carve(&off, sizeof(unsigned) * (nGroups + 1));
   const size_t o_costs = d_costs ? 0 : carve(&off, sizeof(double) * K);
   const size_t o_coll = carve(&off, (size_t)K);
@@ -797,16 +793,15 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   c.d_obst = (double*)(base + o_obst);
   c.d_in = nullptr;
   c.d_part = (float*)(base + o_part);
-  c.d_part_rz = (double2*)(base + o_prz);
+  c.d_part_rz = (float4*)(base + o_prz);
   c.d_gpart = (float*)(base + o_gpart);
-  c.d_gpart_rz = (double2*)(base + o_grz);
+  c.d_gpart_rz = (float4*)(base + o_grz);
   c.d_cnt = (unsigned*)(base + o_cnt);
   c.d_costs = d_costs ? d_costs : (double*)(base + o_costs);
   c.d_coll = (uint8_t*)(base + o_coll);
   c.d_Ustar = (double*)(base + o_Ustar);
   fill_desc(&c);
   c.D.J = J;
-  c.D.TC = c.tl.chunk_steps;
   if (J > 0)
     CK(cudaMemcpyAsync(c.d_obst, d_obst, sizeof(double) * 3 * J, cudaMemcpyDeviceToDevice, s));
   static_prologue<<<1, 256, 0, s>>>(c.D, d_ctl, nGroups + 1);
@@ -816,5 +811,80 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   CK(cudaGetLastError());
   static_epilogue<<<1, 32, 0, s>>>(c.d_st, d_ctl, d_u0);
   CK(cudaGetLastError());
+  return MPPI_OK;
+}
+
+// ------------------------------------------------------------------------
+// Autotuner: time the candidate launch shapes on the problem itself and keep
+// the fastest.  Candidates: samples per CTA in {2, 4, 7, 10, 14, 20, 27, 32}
+// (those giving at most 16 CTAs per SM), threads in {128, 256, 512}, world
+// points per barrier thread in {8, 14, 16} (whole units).  Each candidate runs
+// `iters` steps after two warm-up steps on a scratch controller, timed with
+// CUDA events; the controller state is reset so every candidate sees the same
+// inputs.
+extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J, int32_t iters,
+                             mppi_tiling* best, float* best_us) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!best) return fail(MPPI_EINVAL, "best is NULL");
+  if (iters < 1) iters = 5;
+  const int sms = num_sms();
+  const int S_opts[8] = {2, 4, 7, 10, 14, 20, 27, 32};
+  const int NT_opts[3] = {128, 256, 512};
+  const int NP_opts[3] = {8, 14, 16};
+  const int n = state_dim(p->model);
+  double* x0 = new double[(size_t)n * (p->T + 2)];
+  for (int d = 0; d < n; ++d) x0[d] = p->x_goal[d];
+  for (int t = 0; t <= p->T; ++t)
+    for (int d = 0; d < n; ++d) x0[n + t * n + d] = p->x_goal[d];
+  float best_t = 1e30f;
+  mppi_tiling best_tl = {0, 0, 0, 0};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int S : S_opts) {
+    const long nT = ((long)p->K + S - 1) / S;
+    if (S > p->K && S != S_opts[0]) continue;
+    if (nT > 16L * sms * 4 && S < 32) continue;  // far too many tiny tiles
+    for (int NT : NT_opts)
+      for (int NP : NP_opts) {
+        if (NP < p->n_shape) continue;
+        mppi_tiling t = {S, NT, NP, 0};
+        mppi_ctx* c = nullptr;
+        if (mppi_create_tiled(p, nullptr, &t, &c) != MPPI_OK) continue;
+        if (mppi_set_obstacles(c, cxcyr, J) != MPPI_OK || c->tl.samples_per_cta != S) {
+          mppi_destroy(c);
+          continue;
+        }
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = mppi_step(c, x0, x0 + n, nullptr) == MPPI_OK;
+        if (ok) ok = cudaStreamSynchronize(c->own) == cudaSuccess;
+        float ms = 0.0f;
+        if (ok) {
+          cudaEventRecord(e0, c->own);
+          for (int i = 0; i < iters && ok; ++i)
+            ok = mppi_step_device(c, c->d_in, c->d_in + n, nullptr) == MPPI_OK;
+          cudaEventRecord(e1, c->own);
+          ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+          if (ok) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        mppi_destroy(c);
+        if (!ok) {
+          cudaGetLastError();
+          continue;
+        }
+        const float us = 1000.0f * ms / iters;
+        if (us < best_t) {
+          best_t = us;
+          best_tl = t;
+        }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  delete[] x0;
+  if (best_tl.samples_per_cta == 0) return fail(MPPI_ECUDA, "no launch shape ran");
+  *best = best_tl;
+  if (best_us) *best_us = best_t;
   return MPPI_OK;
 }

@@ -2,27 +2,22 @@
 //
 // One controller's K samples are cut into tiles of S <= 32 samples; a CTA
 // processes one tile (plain step: one CTA per tile; batched step: persistent
-// CTAs pull (controller, tile) work items).  Per tile, for each chunk of TC
-// time steps:
-//   warps 1..   draw the NLN perturbations of the next chunk (Eq. 11) from
-//               Philox4x32-10 with counter (k, t, iter) -- no noise crosses HBM;
-//   warp 0      (lane = sample) clamps v = u + du, steps the dynamics (Eq. 1,
-//               8), accumulates the stage and control costs (Eq. 9), and runs
-//               the DBaS recursion (Eq. 7) of the previous chunk;
-//   all warps   evaluate the fused barrier sum over every (step, sample)
-//               unit, its P shape points and every obstacle (Eq. 5, 13/15):
-//               each thread keeps whole units (NPOS world points) in
-//               registers, streams the obstacle set from shared memory
-//               (broadcast reads) and sums each unit's points exactly into a
-//               float pair.
-// After the horizon the tile forms its own min-shifted exponentiated weights
-// and weighted perturbation sums (the numerator and denominator of Eq. 4
-// relative to the tile's own minimum).  Tiles are combined by a two-level
-// last-arriver reduction (atomic tickets, no spinning): the last CTA of each
-// group of tiles merges the group, and the last group merger forms U*,
-// runs the nominal rollout of U* for C_B (Algorithm 1), sets S_e (Eq. 10) and
-// shifts the sequence.
-//
+// CTAs pull (controller, tile) work items).  Per tile:
+//   noise      all threads draw the NLN perturbations of every (sample, step)
+//              (Eq. 11) from Philox4x32-10 with counter (k, t, iter) -- no
+//              noise crosses HBM -- and keep the clamped controls v = u + du;
+//   dynamics   one warp per sample, lanes over steps: explicit Euler for both
+//              models is triangular (heading rate -> heading -> velocities
+//              -> positions), so a whole trajectory is a few warp prefix
+//              scans over time, segment by segment, with one sincos per step;
+//              the warp also sums the stage and control costs (Eq. 9);
+//   barrier    all threads evaluate the fused barrier sum over every
+//              (step, sample) unit, its P shape points and every obstacle
+//              (Eq. 5, 13/15): each thread keeps whole units (NPOS world
+//              points) in registers, streams the obstacle set from shared
+//              memory (broadcast reads) and sums each unit's points exactly
+//              into a float pair, written over the unit's pose;
+//   costs      one warp per sample adds the barrier-state and collision costs.
 // The DBaS recursion of Eq. 7, w_t = b_t + gamma (w_{t-1} - beta_d), is
 // linear, so its cost sum is evaluated in unrolled form:
 //   sum_{t=1..T} w_t = sum_s c_s b_s + beta_0 g1 - gamma beta_d csum,
@@ -71,12 +66,12 @@ struct DevState {
 // Everything a CTA needs to process one tile of one controller.
 struct CtrlDesc {
   int model, K, T, J, P, n;
-  int S, TC, NPOS, nTiles, GT, nGroups;
+  int S, NPOS, nTiles, GT, nGroups;
   float dt, h_eps, gamma_bas_f, R_B, C_coll, ln_mu, ln_sigma;
   float umin[2], umax[2];
   float Q[kMaxN], Qf[kMaxN];
   float shape[2 * kMaxShape];
-  float g, inv_mass, arm_over_I;
+  float g, inv_mass, arm_over_I, inv_lambda_f;
   double lambda, inv_lambda, mu_coarse, gamma_ctrl, gamma_bas, R_B_d;
   double umin_d[2], umax_d[2];
   int nscl;
@@ -94,9 +89,9 @@ struct CtrlDesc {
   const double* x0;          // n (may be overridden per launch)
   const double* xref;        // (T+1) x n
   float* part;               // nTiles x 2T tile weighted sums
-  double2* part_rz;          // nTiles x (rho_c, Z_c)
+  float4* part_rz;           // nTiles x (rho_c hi, lo, Z_c hi, lo), rho relative to base
   float* gpart;              // nGroups x 2T
-  double2* gpart_rz;         // nGroups
+  float4* gpart_rz;          // nGroups
   unsigned* counters;        // nGroups + 1 tickets (zero between steps)
   double* costs;             // K
   uint8_t* coll;             // K
@@ -104,43 +99,42 @@ struct CtrlDesc {
 };
 
 // Shared-memory layout of one tile; host and device compute it alike.
-// region: per-chunk poses + whole-horizon perturbations + per-position
-// barrier partials, reused as the raw obstacle staging buffer before the
-// rollout and as the nominal-rollout buffers in the final stage.
+// region: poses (overwritten in place by the unit barrier sums) and clamped
+// controls of the whole horizon; reused as the raw obstacle staging buffer
+// before the rollout, as the per-warp column sums of a merge and as the
+// nominal-rollout buffers in the final stage.
 struct SmemLayout {
-  int obs4, region, dU, pose, posB, Uf, Af, red, Us, Usf, colhi, collo, scl, xrf, shp, eS, cw,
-      total;
+  int obs4, region, pose, V, red, Us, Usf, Uf, Af, colhi, collo, scl, xrf, shp, eS, cw, Sk, scH,
+      scL, collf, xi, total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, int J, int n,
-                                                  int nscl, int nwarps) {
+__host__ __device__ inline SmemLayout smem_layout(int T, int S, int P, int J, int n, int nscl,
+                                                  int nwarps) {
   SmemLayout L;
   int off = 0;
   L.obs4 = off;
   off += 16 * (J > 0 ? J : 1);
   off = align_up(off, 16);
   L.region = off;
-  int pose_b = 16 * TC * S;
-  int dU_b = 8 * T * S;
-  int uB_b = 8 * TC * S;
-  int main_b = pose_b + dU_b + uB_b;
+  int main_b = 16 * T * S + 8 * T * S;
   int raw_b = align_up(24 * J, 16);
-  int nom_b = 16 * T + 8 * T;
-  int merge_b = 8 * 2 * T * nwarps;  // per-warp float-pair column sums of a merge
+  int nom_b = 16 * T + 4 * T * P;
+  int merge_b = 8 * 2 * T * nwarps;
   int reg = main_b;
   if (raw_b > reg) reg = raw_b;
   if (nom_b > reg) reg = nom_b;
   if (merge_b > reg) reg = merge_b;
   L.pose = off;
-  L.dU = off + pose_b;
-  L.posB = off + pose_b + dU_b;
+  L.V = off + 16 * T * S;
   off += align_up(reg, 16);
   L.red = off;
   off += 8 * 4 * 32;
   L.Us = off;
   off += 16 * T;
+  L.Sk = off;
+  off += 8 * 32;
   L.Usf = off;
   off += 8 * T;
   L.Uf = off;
@@ -162,6 +156,14 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int TC, int P, i
   off += 4 * 32;
   L.cw = off;
   off += 4 * T;
+  L.scH = off;
+  off += 4 * 32;
+  L.scL = off;
+  off += 4 * 32;
+  L.xi = off;
+  off += 4 * kMaxN;
+  L.collf = off;
+  off += 32;
   L.total = align_up(off, 16);
   return L;
 }
@@ -222,6 +224,38 @@ __device__ __forceinline__ void ff_add(FF& a, float x) {
   a.lo = __fadd_rn(a.lo, e);
 }
 
+// TwoProd: c * (bh + bl) = ph + pe (+ c bl) added to the float pair.
+__device__ __forceinline__ void ff_add_prod(FF& a, float c, float bh, float bl) {
+  float ph = c * bh;
+  float pe = fmaf(c, bh, -ph);
+  ff_add(a, ph);
+  a.lo += fmaf(c, bl, pe);
+}
+
+// Renormalise a float pair so that |lo| <= ulp(hi) / 2 (Fast2Sum).
+__device__ __forceinline__ FF ff_norm(FF a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  return FF{s, __fsub_rn(a.lo, __fsub_rn(s, a.hi))};
+}
+// Lexicographic order of normalised float pairs = order of their values.
+__device__ __forceinline__ bool ff_less(FF a, FF b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+// (a - b) rounded to float, for normalised pairs a >= b.
+__device__ __forceinline__ float ff_diff(FF a, FF b) {
+  return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+__device__ __forceinline__ FF warp_min_ff(FF a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    if (ff_less(b, a)) a = b;
+  }
+  return a;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -277,52 +311,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
 }
 
 // ------------------------------------------------------------------ dynamics
-// State in registers; (cs, sn) are cos/sin of the current heading and are
-// refreshed to the new heading by each step (they also place the shape points).
+// State dimension of each model (the Euler steps themselves are evaluated in
+// scan form, see scan_trajectory).
 template <int MODEL>
-struct Dyn;
-
-template <>
-struct Dyn<0> {  // unicycle (x, y, theta), u = (v, omega)
-  static constexpr int n = 3;
-  __device__ __forceinline__ static void step(float* x, float& cs, float& sn, float v0, float v1,
-                                              const CtrlDesc& D) {
-    float vdt = v0 * D.dt;
-    x[0] = fmaf(vdt, cs, x[0]);
-    x[1] = fmaf(vdt, sn, x[1]);
-    x[2] = fmaf(v1, D.dt, x[2]);
-    sincosf(x[2], &sn, &cs);
-  }
-};
-
-template <>
-struct Dyn<1> {  // planar quadrotor (y, z, phi, ydot, zdot, phidot), u = thrust deviations
-  static constexpr int n = 6;
-  __device__ __forceinline__ static void step(float* x, float& cs, float& sn, float v0, float v1,
-                                              const CtrlDesc& D) {
-    float dt = D.dt;
-    float acc = fmaf(v0 + v1, D.inv_mass, D.g);  // (F1 + F2) / m
-    float y = fmaf(x[3], dt, x[0]);
-    float z = fmaf(x[4], dt, x[1]);
-    float ph = fmaf(x[5], dt, x[2]);
-    float vy = fmaf(-acc * sn, dt, x[3]);
-    float vz = fmaf(fmaf(acc, cs, -D.g), dt, x[4]);
-    float w = fmaf((v1 - v0) * D.arm_over_I, dt, x[5]);
-    x[0] = y;
-    x[1] = z;
-    x[2] = ph;
-    x[3] = vy;
-    x[4] = vz;
-    x[5] = w;
-    sincosf(ph, &sn, &cs);
-  }
+struct Dyn {
+  static constexpr int n = MODEL == 0 ? 3 : 6;
 };
 
 // ------------------------------------------------------------ tile kernel body
 struct TileScratch {
   uint64_t mbar;
   int flag;
-  double beta0, beta_d, Kconst;
+  double beta0, beta_d, Kconst, base;  // base = C0 + Kconst
+  FF rho, Z;                           // merge results
 };
 
 // Fused barrier over nunits (step, sample) units; unit u has pose pose[u]
@@ -330,14 +331,15 @@ struct TileScratch {
 // time (NPOS >= P), keeps their world points in registers and streams every
 // obstacle: h = |p - c|^2 - r^2 evaluated as fma(dx, dx, fma(dy, dy, -r^2)),
 // term 1 / max(h, h_eps) by the approximate reciprocal.  A unit's points are
-// summed exactly (TwoSum) into (hi, lo); the sign bit of hi marks a unit in
-// which some h <= 0 (collision).
+// summed exactly (TwoSum) into (hi, lo), stored at uB[u * ustride]; the sign
+// bit of hi marks a unit in which some h <= 0 (collision).  A thread reads
+// the poses of its units before it writes their sums, so uB may overlay
+// pose.
 template <int NPOS>
-__device__ __forceinline__ void barrier_units(int nunits, int P, int J,
-                                              const float4* __restrict__ pose,
+__device__ __forceinline__ void barrier_units(int nunits, int P, int J, const float4* pose,
                                               const float2* __restrict__ shp,
                                               const float4* __restrict__ obs4, float h_eps,
-                                              float2* __restrict__ uB, int tid, int nthreads) {
+                                              float2* uB, int ustride, int tid, int nthreads) {
   const int upt = NPOS / P;  // units per thread per round
   const int used = upt * P;
   for (int ub = tid * upt; ub < nunits; ub += nthreads * upt) {
@@ -380,7 +382,7 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J,
         coll |= (mn[i] <= 0.0f);
         if (++p == P) {
           const int u = ub + uu;
-          if (u < nunits) uB[u] = make_float2(coll ? -f.hi : f.hi, f.lo);
+          if (u < nunits) uB[(size_t)u * ustride] = make_float2(coll ? -f.hi : f.hi, f.lo);
           f.hi = 0.0f;
           f.lo = 0.0f;
           coll = false;
@@ -400,59 +402,102 @@ __device__ __forceinline__ FF ff_sum(FF a, FF b) {
   return r;
 }
 
+// Sum of a float pair over the 32 lanes (fixed butterfly order).
+__device__ __forceinline__ FF warp_sum_ff(FF a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a = ff_sum(a, b);
+  }
+  return a;
+}
+
 // Merge n partial results (rho_i, Z_i, cols_i[ncol]) taken relative to their
 // own minima into one relative to the common minimum: the log-sum-exp merge
 // of Eq. 4's numerator and denominator.  Warp w takes sources w, w + nwarps,
-// ...; lane l takes columns l, l + 32, ... (ncol <= 32 * kMaxColsPerLane), so
-// every load instruction reads a contiguous row segment and many rows are in
-// flight at once; the per-warp float-pair sums are then added in warp order.
-// All threads of the CTA call it.  buf: nwarps x ncol float pairs.
-// Outputs in shared memory: *rho_out, *Z_out, col_hi/col_lo[ncol].
+// ...; lane l takes columns l, l + 32, ... (ncol <= 32 * kMaxColsPerLane).
+// Every load (the sources' minima and normalisers, and batches of whole rows)
+// is issued before the first value is used, so the merge costs about one
+// round trip to L2 per batch; the per-warp float-pair sums are then added in
+// warp order.  The normaliser is summed as a float pair.  All threads of the
+// CTA call it.  buf: nwarps x ncol float pairs.  Outputs in shared memory:
+// *rho_out, *Z_out, col_hi/col_lo[ncol].
 constexpr int kMaxColsPerLane = 16;  // 2 T <= 512
-__device__ inline void merge_partials(int n, const double2* rz, const float* cols, int ncol,
-                                      double inv_lambda, float* scl, double* rho_out,
-                                      double* Z_out, float* col_hi, float* col_lo, FF* buf,
-                                      double* red, int tid, int nthreads) {
+constexpr int kMergeLoads = 32;      // loads in flight per lane
+template <int NJ>  // column slots per lane: ncol <= 32 NJ
+__device__ inline void merge_partials_nj(int n, const float4* rz, const float* cols, int ncol,
+                                         float inv_lambda, float* scl, FF* rho_out, FF* Z_out,
+                                         float* col_hi, float* col_lo, FF* buf, int tid,
+                                         int nthreads) {
+  constexpr int RPB = kMergeLoads / NJ;  // rows per batch per warp
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-  if (warp == 0) {
-    double r = __longlong_as_double(0x7ff0000000000000ll);
-    for (int i = lane; i < n; i += 32) r = fmin(r, __ldcg(&rz[i].x));
-    r = warp_min_d(r);
-    double z = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      double2 v = __ldcg(&rz[i]);
-      float s = expf(-(float)((v.x - r) * inv_lambda));
-      scl[i] = s;
-      z += v.y * (double)s;
+  float v[kMergeLoads];
+  int i0 = warp;
+  auto load_batch = [&](int first) {
+#pragma unroll
+    for (int q = 0; q < kMergeLoads; ++q) {
+      const int r = q / NJ, j = q % NJ;
+      const int i = first + r * nwarps;
+      const int c = lane + 32 * j;
+      v[q] = (i < n && c < ncol) ? __ldcg(cols + (size_t)i * ncol + c) : 0.0f;
     }
-    z = warp_sum_d(z);
+  };
+  load_batch(i0);  // issued before the minima are known
+  if (warp == 0) {
+    const float inf = __int_as_float(0x7f800000);
+    const float4 a = lane < n ? __ldcg(&rz[lane]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
+    const float4 b = lane + 32 < n ? __ldcg(&rz[lane + 32]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
+    FF r = FF{a.x, a.y};
+    if (ff_less(FF{b.x, b.y}, r)) r = FF{b.x, b.y};
+    for (int i = lane + 64; i < n; i += 32) {
+      const float4 c = __ldcg(&rz[i]);
+      if (ff_less(FF{c.x, c.y}, r)) r = FF{c.x, c.y};
+    }
+    r = warp_min_ff(r);
+    FF z = {0.0f, 0.0f};
+    if (lane < n) {
+      const float sc = expf(-ff_diff(FF{a.x, a.y}, r) * inv_lambda);
+      scl[lane] = sc;
+      ff_add_prod(z, sc, a.z, a.w);
+    }
+    if (lane + 32 < n) {
+      const float sc = expf(-ff_diff(FF{b.x, b.y}, r) * inv_lambda);
+      scl[lane + 32] = sc;
+      ff_add_prod(z, sc, b.z, b.w);
+    }
+    for (int i = lane + 64; i < n; i += 32) {
+      const float4 c = __ldcg(&rz[i]);
+      const float sc = expf(-ff_diff(FF{c.x, c.y}, r) * inv_lambda);
+      scl[i] = sc;
+      ff_add_prod(z, sc, c.z, c.w);
+    }
+    z = warp_sum_ff(z);
     if (lane == 0) {
       *rho_out = r;
-      *Z_out = z;
+      *Z_out = ff_norm(z);
     }
   }
   __syncthreads();
-  FF acc[kMaxColsPerLane];
+  FF acc[NJ];
 #pragma unroll
-  for (int j = 0; j < kMaxColsPerLane; ++j) acc[j].hi = acc[j].lo = 0.0f;
-  const int nj = (ncol + 31) / 32;
-  for (int i = warp; i < n; i += nwarps) {
-    const float s = scl[i];
-    const float* row = cols + (size_t)i * ncol;
-    float v[kMaxColsPerLane];
+  for (int j = 0; j < NJ; ++j) acc[j].hi = acc[j].lo = 0.0f;
+  for (;;) {
 #pragma unroll
-    for (int j = 0; j < kMaxColsPerLane; ++j) {
-      int c = lane + 32 * j;
-      v[j] = (j < nj && c < ncol) ? __ldcg(row + c) : 0.0f;
+    for (int q = 0; q < kMergeLoads; ++q) {
+      const int r = q / NJ, j = q % NJ;
+      const int i = i0 + r * nwarps;
+      if (i < n) ff_add(acc[j], v[q] * scl[i]);
     }
-#pragma unroll
-    for (int j = 0; j < kMaxColsPerLane; ++j)
-      if (j < nj) ff_add(acc[j], v[j] * s);
+    i0 += RPB * nwarps;
+    if (i0 >= n) break;
+    load_batch(i0);
   }
 #pragma unroll
-  for (int j = 0; j < kMaxColsPerLane; ++j) {
-    int c = lane + 32 * j;
-    if (j < nj && c < ncol) buf[warp * ncol + c] = acc[j];
+  for (int j = 0; j < NJ; ++j) {
+    const int c = lane + 32 * j;
+    if (c < ncol) buf[warp * ncol + c] = acc[j];
   }
   __syncthreads();
   for (int c = tid; c < ncol; c += nthreads) {
@@ -461,8 +506,66 @@ __device__ inline void merge_partials(int n, const double2* rz, const float* col
     col_hi[c] = a.hi;
     col_lo[c] = a.lo;
   }
-  (void)red;
   __syncthreads();
 }
+
+__device__ inline void merge_partials(int n, const float4* rz, const float* cols, int ncol,
+                                      float inv_lambda, float* scl, FF* rho_out, FF* Z_out,
+                                      float* col_hi, float* col_lo, FF* buf, int tid,
+                                      int nthreads) {
+  const int nj = (ncol + 31) / 32;
+  if (nj <= 1)
+    merge_partials_nj<1>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+  else if (nj <= 2)
+    merge_partials_nj<2>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+  else if (nj <= 4)
+    merge_partials_nj<4>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+  else if (nj <= 8)
+    merge_partials_nj<8>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+  else
+    merge_partials_nj<16>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+}
+
+// Fused barrier over npos positions, one position per thread at a time
+// (position i = unit i / P, shape point i % P): the fully parallel form used
+// for the single nominal trajectory.  out[i] = +-sum_j 1/max(h, h_eps), the
+// sign bit marking some h <= 0.
+__device__ __forceinline__ void barrier_flat(int npos, int P, int J, const float4* __restrict__ pose,
+                                             const float2* __restrict__ shp,
+                                             const float4* __restrict__ obs4, float h_eps,
+                                             float* __restrict__ out, int tid, int nthreads) {
+  for (int i = tid; i < npos; i += nthreads) {
+    const int u = i / P, p = i - u * P;
+    const float4 ps = pose[u];
+    const float2 sh = shp[p];
+    const float X = fmaf(ps.z, sh.x, fmaf(-ps.w, sh.y, ps.x));
+    const float Y = fmaf(ps.w, sh.x, fmaf(ps.z, sh.y, ps.y));
+    float acc = 0.0f, mn = __int_as_float(0x7f800000);
+    for (int j = 0; j < J; ++j) {
+      const float4 o = obs4[j];
+      float dx = X - o.x, dy = Y - o.y;
+      float h = fmaf(dx, dx, fmaf(dy, dy, o.z));
+      mn = fminf(mn, h);
+      acc += rcp_approx(fmaxf(h, h_eps));
+    }
+    out[i] = mn <= 0.0f ? -acc : acc;
+  }
+}
+
+// Warp inclusive prefix sum over the 32 lanes.
+__device__ __forceinline__ float warp_incl_scan(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+// The value of lane - 1; lane 0 receives `first`.
+__device__ __forceinline__ float from_prev_lane(float v, float first, int lane) {
+  float y = __shfl_up_sync(0xffffffffu, v, 1);
+  return lane == 0 ? first : y;
+}
+__device__ __forceinline__ float lane31(float v) { return __shfl_sync(0xffffffffu, v, 31); }
 
 }  // namespace dbm

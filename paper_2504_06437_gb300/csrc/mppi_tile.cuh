@@ -14,13 +14,6 @@ constexpr int kTmaPolls = 1 << 22;
 #define DBM_STAGE_TMA 1
 #endif
 
-// TwoProd: c * b = ph + pe exactly, added to the float pair.
-__device__ __forceinline__ void ff_add_prod(FF& a, float c, float bh, float bl) {
-  float ph = c * bh;
-  float pe = fmaf(c, bh, -ph);
-  ff_add(a, ph);
-  a.lo += fmaf(c, bl, pe);
-}
 
 // Constants of the controller that never change: the unrolled DBaS weights
 // c_s (scaled by R_B) and their sums.  One CTA, at creation.
@@ -45,115 +38,214 @@ __device__ inline void init_constants(const CtrlDesc& D, int tid, int nthreads) 
 // part of the control cost of Eq. 9 (Algorithm 1 form
 // gamma u^T (S_e Sigma)^-1 v) that every sample shares.  Run by one CTA after
 // each shift, and by a one-CTA kernel after the host sets the state.
-// red: >= 32 doubles of shared memory.
-__device__ inline void prep_constants(const CtrlDesc& D, double* red, int tid, int nthreads) {
+// Usrc: the sequence (shared or global memory); red: >= 32 doubles of shared
+// memory.
+__device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, double* red, int tid,
+                                      int nthreads) {
   DevState* st = D.st;
   const int T = D.T;
   __syncthreads();
-  const double Se = st->S_e;
-  const double inv_Se = 1.0 / Se;
+  const float Se = (float)st->S_e;
+  const float inv_Se = 1.0f / Se;
   if (tid == 0) {
-    const double r = sqrt(Se);
-    st->L00 = (float)(r * D.Lsig[0]);
-    st->L10 = (float)(r * D.Lsig[1]);
-    st->L11 = (float)(r * D.Lsig[2]);
+    const float r = sqrtf(Se);
+    st->L00 = r * (float)D.Lsig[0];
+    st->L10 = r * (float)D.Lsig[1];
+    st->L11 = r * (float)D.Lsig[2];
   }
-  const double M00 = D.Sinv[0] * inv_Se, M01 = D.Sinv[1] * inv_Se;
-  const double M10 = D.Sinv[2] * inv_Se, M11 = D.Sinv[3] * inv_Se;
-  double c0 = 0.0;
+  const float M00 = (float)D.Sinv[0] * inv_Se, M01 = (float)D.Sinv[1] * inv_Se;
+  const float M10 = (float)D.Sinv[2] * inv_Se, M11 = (float)D.Sinv[3] * inv_Se;
+  FF c0 = {0.0f, 0.0f};
   for (int t = tid; t < T; t += nthreads) {
-    double u0 = D.U[2 * t], u1 = D.U[2 * t + 1];
-    double a0 = M00 * u0 + M01 * u1, a1 = M10 * u0 + M11 * u1;
-    D.cU[t] = make_float2((float)u0, (float)u1);
-    D.cA[t] = make_float2((float)a0, (float)a1);
-    c0 += u0 * a0 + u1 * a1;
+    const float u0 = (float)Usrc[2 * t], u1 = (float)Usrc[2 * t + 1];
+    const float a0 = fmaf(M00, u0, M01 * u1), a1 = fmaf(M10, u0, M11 * u1);
+    D.cU[t] = make_float2(u0, u1);
+    D.cA[t] = make_float2(a0, a1);
+    ff_add_prod(c0, u0, a0, 0.0f);
+    ff_add_prod(c0, u1, a1, 0.0f);
   }
-  c0 = warp_sum_d(c0);
-  if ((tid & 31) == 0) red[tid >> 5] = c0;
+  c0 = warp_sum_ff(c0);
+  float* redf = reinterpret_cast<float*>(red);
+  if ((tid & 31) == 0) {
+    redf[2 * (tid >> 5)] = c0.hi;
+    redf[2 * (tid >> 5) + 1] = c0.lo;
+  }
   __syncthreads();
   if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < (nthreads >> 5); ++w) sum += red[w];
-    st->C0 = sum;
+    FF sum = {0.0f, 0.0f};
+    for (int w = 0; w < (nthreads >> 5); ++w) sum = ff_sum(sum, FF{redf[2 * w], redf[2 * w + 1]});
+    st->C0 = (double)sum.hi + (double)sum.lo;
   }
   __syncthreads();
 }
 
-// Barrier-state cost of one trajectory from its unit sums uB[0..T): the
-// sample-dependent part sum_s R_B c_s b_s, spread over the lanes of one warp
-// (all lanes call it), plus the FP64 constant.
-__device__ __forceinline__ double dbas_cost_warp(const float2* uB, const float* cw, int T,
-                                                 double Kconst, int lane) {
-  FF a = {0.0f, 0.0f};
-  for (int t = lane; t < T; t += 32) {
-    float2 v = uB[t];
-    ff_add_prod(a, cw[t], fabsf(v.x), v.y);
-  }
+// One trajectory of T explicit-Euler steps (Eq. 1, 12) under the controls
+// V[t * vs], from the initial state x_init (position rebased to the origin),
+// evaluated by the 32 lanes of one warp: lanes take steps t = t0 + lane in
+// segments of 32, and every state component is a prefix sum over steps of
+// increments that depend only on components earlier in the chain
+//   unicycle:  theta -> (cos, sin) -> (x, y)
+//   quadrotor: phidot -> phi -> (cos, sin) -> (ydot, zdot) -> (y, z)
+// so each segment is a few warp scans, carried from segment to segment.  The
+// pose after step t is written to pose[t * ps] as (x, y, cos, sin) of the
+// heading.  With COST the lane also adds to `cost` its steps' stage cost
+// q(x_{t+1}) and control cost a_t . (v_t - u_t) of Eq. 9 (Algorithm 1 form,
+// the sample-independent part u_t . a_t excluded), and phi(x_T).
+template <int MODEL, bool COST>
+__device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int vs,
+                                const float* __restrict__ x_init, float4* pose, int ps,
+                                const float2* __restrict__ Uf, const float2* __restrict__ Af,
+                                const float* __restrict__ xrf, FF& cost, int lane) {
+  const float dt = D.dt;
+  if constexpr (MODEL == 0) {
+    float cth = x_init[2], cx = x_init[0], cy = x_init[1];
+    float cs_, cc_;
+    sincosf(cth, &cs_, &cc_);
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const bool valid = t < T;
+      const float2 v = valid ? V[t * vs] : make_float2(0.0f, 0.0f);
+      const float th_a = cth + warp_incl_scan(v.y * dt, lane);
+      float sa, ca;
+      sincosf(th_a, &sa, &ca);
+      const float cb = from_prev_lane(ca, cc_, lane), sb = from_prev_lane(sa, cs_, lane);
+      const float vdt = v.x * dt;
+      const float xa = cx + warp_incl_scan(vdt * cb, lane);
+      const float ya = cy + warp_incl_scan(vdt * sb, lane);
+      if (valid) {
+        pose[t * ps] = make_float4(xa, ya, ca, sa);
+        if constexpr (COST) {
+          const float* xr = xrf + (t + 1) * 3;
+          const float e0 = xa - xr[0], e1 = ya - xr[1], e2 = th_a - xr[2];
+          ff_add(cost, fmaf(D.Q[0] * e0, e0, fmaf(D.Q[1] * e1, e1, D.Q[2] * e2 * e2)));
+          const float2 u = Uf[t], a = Af[t];
+          ff_add(cost, fmaf(a.x, v.x - u.x, a.y * (v.y - u.y)));
+          if (t == T - 1) {
+            const float* xT = xrf + T * 3;
+            const float f0 = xa - xT[0], f1 = ya - xT[1], f2 = th_a - xT[2];
+            ff_add(cost, fmaf(D.Qf[0] * f0, f0, fmaf(D.Qf[1] * f1, f1, D.Qf[2] * f2 * f2)));
+          }
+        }
+      }
+      cth = lane31(th_a);
+      cc_ = lane31(ca);
+      cs_ = lane31(sa);
+      cx = lane31(xa);
+      cy = lane31(ya);
+    }
+  } else {
+    float cy = x_init[0], cz = x_init[1], cph = x_init[2];
+    float cvy = x_init[3], cvz = x_init[4], cw = x_init[5];
+    float cs_, cc_;
+    sincosf(cph, &cs_, &cc_);
+    const float kw = D.arm_over_I * dt;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const bool valid = t < T;
+      const float2 v = valid ? V[t * vs] : make_float2(0.0f, 0.0f);
+      const float w_a = cw + warp_incl_scan((v.y - v.x) * kw, lane);  // phidot_{t+1}
+      const float w_b = from_prev_lane(w_a, cw, lane);                // phidot_t
+      const float ph_a = cph + warp_incl_scan(w_b * dt, lane);        // phi_{t+1}
+      float sa, ca;
+      sincosf(ph_a, &sa, &ca);
+      const float cb = from_prev_lane(ca, cc_, lane), sb = from_prev_lane(sa, cs_, lane);
+      const float acc = fmaf(v.x + v.y, D.inv_mass, D.g);  // (F1 + F2) / m
+      const float vy_a = cvy + warp_incl_scan(-acc * sb * dt, lane);
+      const float vz_a = cvz + warp_incl_scan(fmaf(acc, cb, -D.g) * dt, lane);
+      const float vy_b = from_prev_lane(vy_a, cvy, lane), vz_b = from_prev_lane(vz_a, cvz, lane);
+      const float y_a = cy + warp_incl_scan(vy_b * dt, lane);
+      const float z_a = cz + warp_incl_scan(vz_b * dt, lane);
+      if (valid) {
+        pose[t * ps] = make_float4(y_a, z_a, ca, sa);
+        if constexpr (COST) {
+          const float xs[6] = {y_a, z_a, ph_a, vy_a, vz_a, w_a};
+          const float* xr = xrf + (t + 1) * 6;
+          float q = 0.0f;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    FF b;
-    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-    a = ff_sum(a, b);
+          for (int d = 0; d < 6; ++d) {
+            const float e = xs[d] - xr[d];
+            q = fmaf(D.Q[d] * e, e, q);
+          }
+          ff_add(cost, q);
+          const float2 u = Uf[t], a = Af[t];
+          ff_add(cost, fmaf(a.x, v.x - u.x, a.y * (v.y - u.y)));
+          if (t == T - 1) {
+            const float* xT = xrf + T * 6;
+            float f = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+              const float e = xs[d] - xT[d];
+              f = fmaf(D.Qf[d] * e, e, f);
+            }
+            ff_add(cost, f);
+          }
+        }
+      }
+      cw = lane31(w_a);
+      cph = lane31(ph_a);
+      cc_ = lane31(ca);
+      cs_ = lane31(sa);
+      cvy = lane31(vy_a);
+      cvz = lane31(vz_a);
+      cy = lane31(y_a);
+      cz = lane31(z_a);
+    }
   }
-  return (double)a.hi + (double)a.lo + Kconst;
 }
 
 // Final stage (one CTA per controller per step): U* from the merged sums
 // (Eq. 4), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"),
 // S_e (Eq. 10, C_B floored at 0 inside the logarithm), shift, state update.
 template <int MODEL, int NPOS>
-__device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
-                            double rho, double Z, const double* __restrict__ x0g) {
-  constexpr int n = Dyn<MODEL>::n;
-  const int tid = threadIdx.x, nthreads = blockDim.x;
+__device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts) {
+  const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31;
   const int T = D.T, P = D.P;
   double* Us = reinterpret_cast<double*>(smem + L.Us);
   float2* Usf = reinterpret_cast<float2*>(smem + L.Usf);
   const float* col_hi = reinterpret_cast<const float*>(smem + L.colhi);
   const float* col_lo = reinterpret_cast<const float*>(smem + L.collo);
   float4* pose_nom = reinterpret_cast<float4*>(smem + L.region);
-  float2* uB_nom = reinterpret_cast<float2*>(smem + L.region + 16 * T);
+  float* b_nom = reinterpret_cast<float*>(smem + L.region + 16 * T);
   const float2* shp = reinterpret_cast<const float2*>(smem + L.shp);
   const float4* obs4 = reinterpret_cast<const float4*>(smem + L.obs4);
   const float* cw = reinterpret_cast<const float*>(smem + L.cw);
+  const float* xi = reinterpret_cast<const float*>(smem + L.xi);
+  const double Z = (double)ts.Z.hi + (double)ts.Z.lo;
   const double invZ = 1.0 / Z;
   for (int c = tid; c < 2 * T; c += nthreads) {
     int d = c & 1;
     double du = ((double)col_hi[c] + (double)col_lo[c]) * invZ;
-    double u = D.U[c] + du;
+    double u = Us[c] + du;  // Us holds the step's U, prefetched by the prologue
     u = fmin(fmax(u, D.umin_d[d]), D.umax_d[d]);
     Us[c] = u;
     reinterpret_cast<float*>(Usf)[c] = (float)u;
     D.Ustar[c] = u;
   }
   __syncthreads();
-  if (tid == 0) {
-    float x[n];
-    x[0] = 0.0f;
-    x[1] = 0.0f;
-#pragma unroll
-    for (int d = 2; d < n; ++d) x[d] = (float)x0g[d];
-    float sn, cs;
-    sincosf(x[2], &sn, &cs);
-    for (int t = 0; t < T; ++t) {
-      const float2 u = Usf[t];
-      Dyn<MODEL>::step(x, cs, sn, u.x, u.y, D);
-      pose_nom[t] = make_float4(x[0], x[1], cs, sn);
-    }
+  if (tid < 32) {
+    FF none = {0.0f, 0.0f};
+    scan_trajectory<MODEL, false>(D, T, Usf, 1, xi, pose_nom, 1, nullptr, nullptr, nullptr, none,
+                                  lane);
   }
   __syncthreads();
-  barrier_units<NPOS>(T, P, D.J, pose_nom, shp, obs4, D.h_eps, uB_nom, tid, nthreads);
+  barrier_flat(T * P, P, D.J, pose_nom, shp, obs4, D.h_eps, b_nom, tid, nthreads);
   __syncthreads();
   if (tid < 32) {
-    const double CB = dbas_cost_warp(uB_nom, cw, T, ts.Kconst, tid);
+    FF a = {0.0f, 0.0f};
+    for (int t = lane; t < T; t += 32) {
+      FF b = {0.0f, 0.0f};
+      for (int p = 0; p < P; ++p) ff_add(b, fabsf(b_nom[t * P + p]));
+      ff_add_prod(a, cw[t], b.hi, b.lo);
+    }
+    a = warp_sum_ff(a);
+    const double CB = (double)a.hi + (double)a.lo + ts.Kconst;
     if (tid == 0) {
       DevState* st = D.st;
       const double S_e_used = st->S_e;
       // Eq. 10, C_B floored at 0 inside the logarithm
       const float arg = (float)(2.718281828459045 + fmax(CB, 0.0));
       const double S_e_next = D.mu_coarse > 0.0 ? D.mu_coarse * (double)logf(arg) : 1.0;
-      st->rho = rho;
+      st->rho = ts.base + ((double)ts.rho.hi + (double)ts.rho.lo);
       st->Z = Z;
       st->CB_star = CB;
       st->beta_used = ts.beta0;
@@ -168,12 +260,14 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
     }
   }
   // shift (Algorithm 1, last loop): u_{t-1} <- u*_t, the last entry kept
+  double* Ush = reinterpret_cast<double*>(smem + L.colhi);  // column sums are consumed
   for (int c = tid; c < 2 * T; c += nthreads) {
     int t = c >> 1, d = c & 1;
-    D.U[c] = (t + 1 < T) ? Us[2 * (t + 1) + d] : Us[2 * (T - 1) + d];
+    const double u = (t + 1 < T) ? Us[2 * (t + 1) + d] : Us[2 * (T - 1) + d];
+    D.U[c] = u;
+    Ush[c] = u;
   }
-  __threadfence_block();
-  prep_constants(D, reinterpret_cast<double*>(smem + L.red), tid, nthreads);
+  prep_constants(D, Ush, reinterpret_cast<double*>(smem + L.red), tid, nthreads);
 }
 
 // One tile of one controller.  ts.mbar must be initialised; mbar_phase is
@@ -185,18 +279,22 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
   constexpr int n = Dyn<MODEL>::n;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-  const int T = D.T, S = D.S, P = D.P, J = D.J, TC = D.TC, K = D.K;
-  const SmemLayout L = smem_layout(T, S, TC, P, J, n, D.nscl, nwarps);
+  const int T = D.T, S = D.S, P = D.P, J = D.J, K = D.K;
+  const SmemLayout L = smem_layout(T, S, P, J, n, D.nscl, nwarps);
   float4* obs4 = reinterpret_cast<float4*>(smem + L.obs4);
   float4* pose = reinterpret_cast<float4*>(smem + L.pose);
-  float2* dU = reinterpret_cast<float2*>(smem + L.dU);
-  float2* uB = reinterpret_cast<float2*>(smem + L.posB);
+  float2* uB = reinterpret_cast<float2*>(smem + L.pose);  // overlays pose, stride 2
+  float2* V = reinterpret_cast<float2*>(smem + L.V);
   float2* Uf = reinterpret_cast<float2*>(smem + L.Uf);
   float2* Af = reinterpret_cast<float2*>(smem + L.Af);
   float* xrf = reinterpret_cast<float*>(smem + L.xrf);
   float2* shp = reinterpret_cast<float2*>(smem + L.shp);
   float* eS = reinterpret_cast<float*>(smem + L.eS);
   float* cw = reinterpret_cast<float*>(smem + L.cw);
+  float* scH = reinterpret_cast<float*>(smem + L.scH);
+  float* scL = reinterpret_cast<float*>(smem + L.scL);
+  unsigned char* collf = reinterpret_cast<unsigned char*>(smem + L.collf);
+  float* xi = reinterpret_cast<float*>(smem + L.xi);
   double* red = reinterpret_cast<double*>(smem + L.red);
   DevState* st = D.st;
   const int k0 = tile * S;
@@ -209,10 +307,14 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
 #endif
   if (tid < P) shp[tid] = make_float2(D.shape[2 * tid], D.shape[2 * tid + 1]);
   const double ox = x0g[0], oy = x0g[1];
+  if (tid < n) xi[tid] = tid < 2 ? 0.0f : (float)x0g[tid];
+  double* Us = reinterpret_cast<double*>(smem + L.Us);
   for (int t = tid; t < T; t += nthreads) {
     Uf[t] = D.cU[t];
     Af[t] = D.cA[t];
     cw[t] = D.cw[t];
+    Us[2 * t] = D.U[2 * t];  // for the final stage, should this CTA run it
+    Us[2 * t + 1] = D.U[2 * t + 1];
   }
   for (int i = tid; i < (T + 1) * n; i += nthreads) {
     int d = i % n;
@@ -262,188 +364,154 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
   {
     float v0 = warp_sum_f(bd), v1 = warp_sum_f(b0);
     if (lane == 0) {
-      red[2 * warp] = (double)v0;
-      red[2 * warp + 1] = (double)v1;
+      reinterpret_cast<float*>(red)[2 * warp] = v0;
+      reinterpret_cast<float*>(red)[2 * warp + 1] = v1;
     }
   }
-  // noise of chunk 0, all threads
-  const uint32_t it_lo = (uint32_t)(st->iter & 0xffffffffull), it_hi = (uint32_t)(st->iter >> 32);
-  const float L00 = st->L00, L10 = st->L10, L11 = st->L11;
-  auto draw_chunk = [&](int c, int first, int count) {
-    int t0 = c * TC;
-    int TCc = min(TC, T - t0);
-    for (int i = tid - first; i < TCc * S; i += count) {
-      int tl = i / S, s = i - tl * S;
-      int t = t0 + tl;
-      uint4 r = philox4x32_10(make_uint4((uint32_t)(k0 + s), (uint32_t)t, it_lo, it_hi), D.key0,
-                              D.key1);
-      dU[t * S + s] = nln_draw(r, L00, L10, L11, D.ln_mu, D.ln_sigma);
+
+  // ---- noise: every (sample, step) draw, kept as the clamped control
+  {
+    const uint32_t it_lo = (uint32_t)(st->iter & 0xffffffffull);
+    const uint32_t it_hi = (uint32_t)(st->iter >> 32);
+    const float L00 = st->L00, L10 = st->L10, L11 = st->L11;
+    const float lo0 = D.umin[0], hi0 = D.umax[0], lo1 = D.umin[1], hi1 = D.umax[1];
+#pragma unroll 2
+    for (int i = tid; i < T * S; i += nthreads) {
+      const int t = i / S, s = i - t * S;
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)(k0 + s), (uint32_t)t, it_lo, it_hi),
+                                    D.key0, D.key1);
+      const float2 du = nln_draw(r, L00, L10, L11, D.ln_mu, D.ln_sigma);
+      const float2 u = Uf[t];
+      V[i] = make_float2(fminf(fmaxf(u.x + du.x, lo0), hi0), fminf(fmaxf(u.y + du.y, lo1), hi1));
     }
-  };
-  draw_chunk(0, 0, nthreads);
+  }
   __syncthreads();
-  if (tid == 0) {
-    double sbd = 0.0, sb0 = 0.0;
+  // (one lane of the last warp, which has the fewest samples below)
+  if (tid == nthreads - 32) {
+    float fbd = 0.0f, fb0 = 0.0f;
     for (int w = 0; w < nwarps; ++w) {
-      sbd += red[2 * w];
-      sb0 += red[2 * w + 1];
+      fbd += reinterpret_cast<const float*>(red)[2 * w];
+      fb0 += reinterpret_cast<const float*>(red)[2 * w + 1];
     }
+    const double sbd = fbd, sb0 = fb0;
     double beta0 = st->first ? sb0 : sb0 + D.gamma_bas * (st->beta - sbd);
     ts.beta_d = sbd;
     ts.beta0 = beta0;
     // sample-independent part of sum_t R_B w_t (unrolled Eq. 7)
     ts.Kconst = D.R_B_d * (beta0 * st->g1 - D.gamma_bas * sbd * st->csum);
+    ts.base = st->C0 + ts.Kconst;
+  }
+
+  // ---- dynamics and stage/control costs: one warp per sample
+  for (int s = warp; s < S; s += nwarps) {
+    FF c = {0.0f, 0.0f};
+    scan_trajectory<MODEL, true>(D, T, V + s, S, xi, pose + s, S, Uf, Af, xrf, c, lane);
+    c = warp_sum_ff(c);
+    if (lane == 0) {
+      scH[s] = c.hi;
+      scL[s] = c.lo;
+    }
   }
   __syncthreads();
 
-  // ---- rollout over chunks
-  float x[n];
-  float cs = 1.0f, sn = 0.0f;
-  FF acc1 = {0.0f, 0.0f}, acc2 = {0.0f, 0.0f};
-  bool coll = false;
-  if (warp == 0) {
-    x[0] = 0.0f;
-    x[1] = 0.0f;
-#pragma unroll
-    for (int d = 2; d < n; ++d) x[d] = (float)x0g[d];
-    sincosf(x[2], &sn, &cs);
-  }
-  // barrier-state and collision costs of chunk c from its unit sums
-  auto recur_chunk = [&](int c) {
-    int t0 = c * TC;
-    int TCc = min(TC, T - t0);
-    for (int tl = 0; tl < TCc; ++tl) {
-      float2 v = uB[tl * S + lane];
-      bool cl = __float_as_int(v.x) < 0;
-      ff_add_prod(acc2, cw[t0 + tl], fabsf(v.x), v.y);
-      if (cl) ff_add(acc2, D.C_coll);
+  // ---- fused barrier over all (step, sample) units, sums over the poses
+  barrier_units<NPOS>(T * S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid, nthreads);
+  __syncthreads();
+
+  // ---- barrier-state and collision costs: one warp per sample; costs are
+  // kept relative to base = C0 + Kconst (the same for every sample of the
+  // controller, so it cancels in the weights)
+  float* relH = reinterpret_cast<float*>(smem + L.scH);
+  float* relL = reinterpret_cast<float*>(smem + L.scL);
+  for (int s = warp; s < S; s += nwarps) {
+    FF b = {0.0f, 0.0f};
+    bool coll = false;
+    for (int t = lane; t < T; t += 32) {
+      const float2 v = uB[2 * (t * S + s)];
+      const bool cl = __float_as_int(v.x) < 0;
+      ff_add_prod(b, cw[t], fabsf(v.x), v.y);
+      if (cl) ff_add(b, D.C_coll);
       coll |= cl;
     }
-  };
-  const int nchunks = (T + TC - 1) / TC;
-  for (int c = 0; c < nchunks; ++c) {
-    const int t0 = c * TC;
-    const int TCc = min(TC, T - t0);
-    if (warp == 0) {
-      if (lane < S) {
-        if (c > 0) recur_chunk(c - 1);
-        for (int tl = 0; tl < TCc; ++tl) {
-          int t = t0 + tl;
-          float2 u = Uf[t];
-          float2 du = dU[t * S + lane];
-          float v0 = fminf(fmaxf(u.x + du.x, D.umin[0]), D.umax[0]);
-          float v1 = fminf(fmaxf(u.y + du.y, D.umin[1]), D.umax[1]);
-          float e0 = v0 - u.x, e1 = v1 - u.y;
-          dU[t * S + lane] = make_float2(e0, e1);
-          Dyn<MODEL>::step(x, cs, sn, v0, v1, D);
-          pose[tl * S + lane] = make_float4(x[0], x[1], cs, sn);
-          const float* xr = xrf + (t + 1) * n;
-          float q = 0.0f;
-#pragma unroll
-          for (int d = 0; d < n; ++d) {
-            float e = x[d] - xr[d];
-            q = fmaf(D.Q[d] * e, e, q);
-          }
-          float2 a = Af[t];
-          ff_add(acc1, q);
-          ff_add(acc1, fmaf(a.x, e0, a.y * e1));
-        }
-      }
-    } else if (c + 1 < nchunks) {
-      draw_chunk(c + 1, 32, nthreads - 32);
-    }
-    __syncthreads();
-    barrier_units<NPOS>(TCc * S, P, J, pose, shp, obs4, D.h_eps, uB, tid, nthreads);
-    __syncthreads();
-  }
-
-  // ---- per-sample cost, tile weights
-  if (warp == 0) {
-    double Sk = __longlong_as_double(0x7ff0000000000000ll);
-    const bool valid = (lane < S) && (k0 + lane < K);
-    if (lane < S) {
-      recur_chunk(nchunks - 1);
-      const float* xr = xrf + T * n;
-      float phi = 0.0f;
-#pragma unroll
-      for (int d = 0; d < n; ++d) {
-        float e = x[d] - xr[d];
-        phi = fmaf(D.Qf[d] * e, e, phi);
-      }
-      double s = (double)acc1.hi + (double)acc2.hi;
-      s += (double)acc1.lo + (double)acc2.lo;
-      s += st->C0 + ts.Kconst + (double)phi;
-      if (valid) Sk = s;
-    }
-    double rho_c = warp_min_d(Sk);
-    float e = valid ? expf(-(float)((Sk - rho_c) * D.inv_lambda)) : 0.0f;
-    double Zc = warp_sum_d((double)e);
-    eS[lane] = e;
-    if (valid) {
-      D.costs[k0 + lane] = Sk;
-      D.coll[k0 + lane] = coll ? 1 : 0;
-    }
+    b = warp_sum_ff(b);
+    coll = __any_sync(0xffffffffu, coll);
     if (lane == 0) {
-      D.part_rz[tile] = make_double2(rho_c, Zc);
-      __threadfence();
+      FF c = {scH[s], scL[s]};
+      c = ff_norm(ff_sum(c, b));
+      relH[s] = c.hi;
+      relL[s] = c.lo;
+      collf[s] = coll ? 1 : 0;
+    }
+  }
+  __syncthreads();
+
+  // ---- tile weights (Eq. 4 relative to the tile's own minimum)
+  if (warp == 0) {
+    const bool valid = (lane < S) && (k0 + lane < K);
+    const FF Sk = valid ? FF{relH[lane], relL[lane]} : FF{__int_as_float(0x7f800000), 0.0f};
+    const FF rho_c = warp_min_ff(Sk);
+    const float e = valid ? expf(-ff_diff(Sk, rho_c) * D.inv_lambda_f) : 0.0f;
+    const FF z = ff_norm(warp_sum_ff(FF{e, 0.0f}));
+    eS[lane] = e;
+    if (lane == 0) D.part_rz[tile] = make_float4(rho_c.hi, rho_c.lo, z.hi, z.lo);
+    if (valid) {
+      D.costs[k0 + lane] = ts.base + ((double)Sk.hi + (double)Sk.lo);
+      D.coll[k0 + lane] = collf[lane];
     }
   }
   __syncthreads();
   {
     float* prow = D.part + (size_t)tile * 2 * T;
     for (int t = warp; t < T; t += nwarps) {
-      float e = eS[lane];
-      float2 du = lane < S ? dU[t * S + lane] : make_float2(0.0f, 0.0f);
-      float a = warp_sum_f(e * du.x);
-      float b = warp_sum_f(e * du.y);
+      const float e = eS[lane];
+      const float2 u = Uf[t];
+      const float2 v = lane < S ? V[t * S + lane] : u;
+      const float a = warp_sum_f(e * (v.x - u.x));
+      const float b = warp_sum_f(e * (v.y - u.y));
       if (lane == 0) reinterpret_cast<float2*>(prow)[t] = make_float2(a, b);
     }
-    if (lane == 0) __threadfence();  // the writers of the tile's partials
   }
 
-  // ---- two-level last-arriver merge: the writers fenced, then one ticket
+  // ---- two-level last-arriver merge.  The CTA's writes are published by
+  // one thread: barrier, fence, ticket; the last arriver fences again before
+  // the barrier that releases its threads to read the others' partials.
   __syncthreads();
   const int g = tile / D.GT;
   const int m0 = g * D.GT;
   const int members = min(D.GT, D.nTiles - m0);
   if (tid == 0) {
+    __threadfence();
     unsigned tk = atomicAdd(&D.counters[g], 1u);
     ts.flag = (tk == (unsigned)(members - 1));
+    if (ts.flag) __threadfence();
   }
   __syncthreads();
   if (!ts.flag) return;
-  __threadfence();
   float* scl = reinterpret_cast<float*>(smem + L.scl);
   float* col_hi = reinterpret_cast<float*>(smem + L.colhi);
   float* col_lo = reinterpret_cast<float*>(smem + L.collo);
   FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
-  double* mres = red + 100;
   const int ncol = 2 * T;
-  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.inv_lambda, scl,
-                 mres, mres + 1, col_hi, col_lo, mbuf, red, tid, nthreads);
-  bool wrote = false;
-  for (int c = tid; c < ncol; c += nthreads) {
-    D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
-    wrote = true;
-  }
+  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.inv_lambda_f, scl,
+                 &ts.rho, &ts.Z, col_hi, col_lo, mbuf, tid, nthreads);
+  for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
   if (tid == 0) {
-    D.gpart_rz[g] = make_double2(mres[0], mres[1]);
+    D.gpart_rz[g] = make_float4(ts.rho.hi, ts.rho.lo, ts.Z.hi, ts.Z.lo);
     D.counters[g] = 0u;
-    wrote = true;
   }
-  if (wrote) __threadfence();
   __syncthreads();
   if (tid == 0) {
+    __threadfence();
     unsigned tk = atomicAdd(&D.counters[D.nGroups], 1u);
     ts.flag = (tk == (unsigned)(D.nGroups - 1));
+    if (ts.flag) __threadfence();
   }
   __syncthreads();
   if (!ts.flag) return;
-  __threadfence();
-  merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda, scl, mres, mres + 1, col_hi,
-                 col_lo, mbuf, red, tid, nthreads);
+  merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z, col_hi,
+                 col_lo, mbuf, tid, nthreads);
   if (tid == 0) D.counters[D.nGroups] = 0u;
-  final_stage<MODEL, NPOS>(D, smem, L, ts, mres[0], mres[1], x0g);
+  final_stage<MODEL, NPOS>(D, smem, L, ts);
 }
 
 }  // namespace dbm
