@@ -204,6 +204,65 @@ int mppi_step_static(const mppi_params* p, const double* d_obst, int32_t J,
                      const double* d_x0, const double* d_xref, double* d_U,
                      double* d_ctl, double* d_u0, double* d_costs, void* stream);
 
+/* ---- Batched execution.  Many controllers -- mixed model, K, T and
+ * obstacle count -- stepped together by one persistent launch: CTAs pull
+ * (controller, tile) work items, longest first, from a device work table;
+ * the copy-in, the launch and the copy-out are captured in a CUDA graph and
+ * replayed while the set of stepped controllers is unchanged.  Each
+ * controller's results are identical, bit for bit, to those of a context
+ * created with the same launch shape (256 threads per CTA).  Not part of the
+ * paper, which steps one controller. */
+typedef struct mppi_batch mppi_batch;
+
+/* A batch of at most max_ctrl controllers whose device state comes from one
+ * pool of pool_bytes (allocated here).  Errors: MPPI_EINVAL, MPPI_ENOMEM. */
+int mppi_batch_create(int32_t max_ctrl, size_t pool_bytes, mppi_batch** out);
+
+/* Admit a controller: parameters as for mppi_create, launch shape (NULL or
+ * zero fields = automatic; threads is always 256), obstacle set (J x 3,
+ * copied; J may be 0).  *slot receives its id.  MPPI_ENOMEM when no slot is
+ * free or the pool cannot hold its state and obstacles (admission refusal;
+ * nothing changes). */
+int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
+                   const mppi_tiling* tiling, const double* cxcyr, int32_t J,
+                   int32_t* slot);
+
+/* Replace the obstacle set of one controller, as mppi_set_obstacles; a
+ * larger set than the slot holds moves it within the pool (MPPI_ENOMEM if
+ * the pool has no room for the larger copy). */
+int mppi_batch_set_obstacles(mppi_batch* b, int32_t slot, const double* cxcyr,
+                             int32_t J);
+
+/* Release a controller's slot and its pool memory. */
+int mppi_batch_remove(mppi_batch* b, int32_t slot);
+
+/* One iteration of the n listed controllers (each at most once).  x0s:
+ * n x 6 doubles (the first n_state of each row are used); xrefs: NULL, or n
+ * pointers each to a (T+1) x n_state reference or NULL (goal repeated).
+ * Copies the inputs; enqueues the step and returns. */
+int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n,
+                    const double* x0s, const double* const* xrefs, void* stream);
+
+/* u*_0 of the controllers of the last step, in the order listed (n x 2).
+ * Synchronises. */
+int mppi_batch_get_controls(mppi_batch* b, double* u0s, int32_t n);
+
+/* One controller's shifted sequence (T x 2), costs of its last step (K) and
+ * scalars[8] as in mppi_get_debug (any pointer may be NULL).  Synchronises. */
+int mppi_batch_get_state(mppi_batch* b, int32_t slot, double* U, double* costs,
+                         double* scalars);
+
+/* Launch shape and pool bytes of a slot (slot < 0: none) and the pool's free
+ * bytes. */
+int mppi_batch_info(mppi_batch* b, int32_t slot, mppi_tiling* t, uint64_t* bytes,
+                    uint64_t* pool_free_bytes);
+
+/* Enable (default) or disable CUDA-graph capture and replay of the step. */
+int mppi_batch_set_graph(mppi_batch* b, int32_t enable);
+
+/* Release the batch and its pool.  NULL is a no-op. */
+int mppi_batch_destroy(mppi_batch* b);
+
 /* Release everything owned by the context.  NULL is a no-op. */
 int mppi_destroy(mppi_ctx* c);
 

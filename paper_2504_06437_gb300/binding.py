@@ -15,12 +15,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _LIB = os.path.join(_HERE, "libdbasmppi.so")
-_SOURCES = ["csrc/dbasmppi.cu"]
-_DEPS = ["csrc/dbasmppi.cu", "csrc/mppi_device.cuh", "csrc/mppi_tile.cuh"]
+_SOURCES = ["csrc/dbasmppi.cu", "csrc/k_step_u.cu", "csrc/k_step_q.cu", "csrc/k_batch.cu"]
+_DEPS = _SOURCES + ["csrc/mppi_device.cuh", "csrc/mppi_tile.cuh", "csrc/kernels.cuh"]
 HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-shared", "-Xcompiler", "-fPIC"]
+              "-Xcompiler", "-fPIC"]
 
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE = 0, -1, -2, -3, -4, -5
 UNICYCLE, QUAD2D = 0, 1
@@ -43,16 +43,30 @@ def _stale() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the CUDA library in-tree for sm_103a (nvcc cross-compiles
-    without a GPU)."""
+    without a GPU): each translation unit in parallel, then one shared link."""
     if not force and not _stale():
         return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    from concurrent.futures import ThreadPoolExecutor
     extra = os.environ.get("DBASMPPI_NVCC_EXTRA", "").split()
-    cmd = ["nvcc", *NVCC_FLAGS, *extra, "-o", tmp, *[os.path.join(_HERE, s) for s in _SOURCES]]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+    objdir = os.path.join(_HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    tag = os.getpid()
+    objs = [os.path.join(objdir, os.path.basename(src).replace(".cu", f".{tag}.o")) for src in _SOURCES]
+
+    def compile_one(i):
+        cmd = ["nvcc", *NVCC_FLAGS, *extra, "-c", "-o", objs[i], os.path.join(_HERE, _SOURCES[i])]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+
+    with ThreadPoolExecutor(len(_SOURCES)) as ex:
+        list(ex.map(compile_one, range(len(_SOURCES))))
+    tmp = _LIB + f".tmp{tag}"
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs],
+                   check=True)
     os.replace(tmp, _LIB)
+    for o in objs:
+        os.remove(o)
     return _LIB
 
 
@@ -110,6 +124,19 @@ def load():
                                      C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     lib.mppi_autotune.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.c_int32,
                                   C.POINTER(Tiling), C.POINTER(C.c_float)]
+    lib.mppi_batch_create.argtypes = [C.c_int32, C.c_size_t, C.POINTER(vp)]
+    lib.mppi_batch_add.argtypes = [vp, C.POINTER(Params), _dp, C.POINTER(Tiling), _dp, C.c_int32,
+                                   C.POINTER(C.c_int32)]
+    lib.mppi_batch_set_obstacles.argtypes = [vp, C.c_int32, _dp, C.c_int32]
+    lib.mppi_batch_remove.argtypes = [vp, C.c_int32]
+    lib.mppi_batch_step.argtypes = [vp, C.POINTER(C.c_int32), C.c_int32, _dp,
+                                    C.POINTER(_dp), vp]
+    lib.mppi_batch_get_controls.argtypes = [vp, _dp, C.c_int32]
+    lib.mppi_batch_get_state.argtypes = [vp, C.c_int32, _dp, _dp, _dp]
+    lib.mppi_batch_info.argtypes = [vp, C.c_int32, C.POINTER(Tiling), C.POINTER(C.c_uint64),
+                                    C.POINTER(C.c_uint64)]
+    lib.mppi_batch_set_graph.argtypes = [vp, C.c_int32]
+    lib.mppi_batch_destroy.argtypes = [vp]
     lib.mppi_last_error.restype = C.c_char_p
     _lib = lib
     return lib
@@ -273,3 +300,100 @@ class Controller:
     def set_state(self, U, S_e, beta, first, it):
         U = _f64(U).reshape(self.T, 2)
         _check(load().mppi_set_state(self.h, _ptr(U), float(S_e), float(beta), int(bool(first)), int(it)))
+
+
+class Batch:
+    """Many controllers stepped by one persistent launch (mppi_batch_*)."""
+
+    def __init__(self, max_ctrl: int, pool_bytes: int):
+        h = C.c_void_p()
+        _check(load().mppi_batch_create(int(max_ctrl), int(pool_bytes), C.byref(h)))
+        self.h = h
+        self.info = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().mppi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def add(self, cfg: dict, obstacles=None, u_init=None, tiling: dict | None = None) -> int:
+        p = make_params(cfg)
+        T = int(p.T)
+        u = None if u_init is None else _f64(u_init).reshape(T, 2)
+        t = Tiling(**{k: int(v) for k, v in tiling.items()}) if tiling else None
+        ob = _f64(obstacles if obstacles is not None else np.zeros((0, 3))).reshape(-1, 3)
+        slot = C.c_int32()
+        _check(load().mppi_batch_add(self.h, C.byref(p), _ptr(u) if u is not None else None,
+                                     C.byref(t) if t is not None else None,
+                                     _ptr(ob) if ob.size else None, ob.shape[0], C.byref(slot)))
+        self.info[slot.value] = (T, 6 if p.model == QUAD2D else 3, int(p.K))
+        return slot.value
+
+    def set_obstacles(self, slot: int, obstacles):
+        ob = _f64(obstacles).reshape(-1, 3)
+        _check(load().mppi_batch_set_obstacles(self.h, int(slot), _ptr(ob) if ob.size else None,
+                                               ob.shape[0]))
+
+    def remove(self, slot: int):
+        _check(load().mppi_batch_remove(self.h, int(slot)))
+        self.info.pop(slot, None)
+
+    def step(self, slots, x0s, xrefs=None, stream=None):
+        slots = np.ascontiguousarray(slots, dtype=np.int32)
+        n = slots.size
+        X = np.zeros((n, 6))
+        for i, x in enumerate(x0s):
+            x = np.asarray(x, dtype=np.float64).ravel()
+            X[i, : x.size] = x
+        self._keep = []
+        ptrs = None
+        if xrefs is not None:
+            ptrs = (_dp * n)()
+            for i, r in enumerate(xrefs):
+                if r is None:
+                    ptrs[i] = _dp()
+                else:
+                    a = _f64(r)
+                    self._keep.append(a)
+                    ptrs[i] = _ptr(a)
+        self._keep.append(X)
+        _check(load().mppi_batch_step(self.h, slots.ctypes.data_as(C.POINTER(C.c_int32)), n,
+                                      _ptr(X), ptrs, _stream_ptr(stream)))
+        self._n = n
+
+    def controls(self) -> np.ndarray:
+        u = np.zeros((self._n, 2))
+        _check(load().mppi_batch_get_controls(self.h, _ptr(u), self._n))
+        return u
+
+    def state(self, slot: int) -> dict:
+        T, n, K = self.info[slot]
+        U = np.zeros((T, 2))
+        costs = np.zeros(K)
+        sc = np.zeros(8)
+        _check(load().mppi_batch_get_state(self.h, int(slot), _ptr(U), _ptr(costs), _ptr(sc)))
+        return dict(U=U, costs=costs, rho=sc[0], Z=sc[1], CB_star=sc[2], S_e=sc[3],
+                    beta_used=sc[4], beta_d=sc[5], S_e_used=sc[6], iter=int(sc[7]))
+
+    def slot_info(self, slot: int = -1) -> dict:
+        t = Tiling()
+        b = C.c_uint64()
+        f = C.c_uint64()
+        _check(load().mppi_batch_info(self.h, int(slot), C.byref(t), C.byref(b), C.byref(f)))
+        return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
+                    positions_per_thread=t.positions_per_thread, bytes=b.value, pool_free=f.value)
+
+    def set_graph(self, enable: bool):
+        _check(load().mppi_batch_set_graph(self.h, int(bool(enable))))

@@ -5,10 +5,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/dbasmppi.h"
-#include "mppi_tile.cuh"
+#include "kernels.cuh"
 
 using namespace dbm;
 
@@ -34,20 +36,6 @@ int fail(int code, const char* fmt, ...) {
 
 // ------------------------------------------------------------------ kernels
 
-template <int MODEL, int NPOS>
-__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ CtrlDesc D,
-                                                   const double* __restrict__ x0,
-                                                   const double* __restrict__ xref) {
-  extern __shared__ __align__(16) char smem[];
-  __shared__ TileScratch ts;
-  if (threadIdx.x == 0) mbar_init(&ts.mbar);
-  __syncthreads();
-  uint32_t phase = 0u;
-  run_tile<MODEL, NPOS>(D, blockIdx.x, x0, xref, smem, ts, phase);
-}
-
-// Constants of the controller (init != 0, at creation) and the per-step
-// constants of its current state.
 __global__ void prep_kernel(const __grid_constant__ CtrlDesc D, int init) {
   __shared__ double red[64];
   if (init) init_constants(D, threadIdx.x, blockDim.x);
@@ -76,20 +64,14 @@ __global__ void draws_kernel(int K, int T, uint32_t k0, uint32_t k1, uint32_t it
 using StepFn = void (*)(CtrlDesc, const double*, const double*);
 
 StepFn pick_kernel(int model, int npos) {
-  if (model == MPPI_UNICYCLE) {
-    if (npos == 14) return step_kernel<0, 14>;
-    if (npos == 16) return step_kernel<0, 16>;
-    return step_kernel<0, 8>;
-  }
-  if (npos == 14) return step_kernel<1, 14>;
-  if (npos == 16) return step_kernel<1, 16>;
-  return step_kernel<1, 8>;
+  if (model == MPPI_UNICYCLE) return npos == 14 ? step_u14 : step_u8;
+  return npos == 14 ? step_q14 : step_q8;
 }
 
 // World points a barrier thread holds: whole units of P points each; the
 // instantiated sizes are 8, 14 and 16, picked to waste the fewest slots.
 int pick_npos(int P) {
-  const int opts[3] = {8, 14, 16};
+  const int opts[2] = {8, 14};
   int best = 16;
   double best_waste = 2.0;
   for (int o : opts) {
@@ -165,7 +147,7 @@ int max_smem_optin() {
   if (v <= 0) v = 48 * 1024;
   cudaFuncAttributes fa;
   size_t stat = 0;
-  if (cudaFuncGetAttributes(&fa, step_kernel<1, 16>) == cudaSuccess) stat = fa.sharedSizeBytes;
+  if (cudaFuncGetAttributes(&fa, step_q14) == cudaSuccess) stat = fa.sharedSizeBytes;
   else cudaGetLastError();
   return v - (int)align_up((int)stat + 64, 128);
 }
@@ -256,8 +238,8 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
   if (t.threads != 64 && t.threads != 128 && t.threads != 256 && t.threads != 512)
     return fail(MPPI_EINVAL, "threads must be 64, 128, 256 or 512");
   if (t.positions_per_thread <= 0) t.positions_per_thread = pick_npos(p->n_shape);
-  if (t.positions_per_thread != 8 && t.positions_per_thread != 14 && t.positions_per_thread != 16)
-    return fail(MPPI_EINVAL, "positions_per_thread must be 8, 14 or 16");
+  if (t.positions_per_thread != 8 && t.positions_per_thread != 14)
+    return fail(MPPI_EINVAL, "positions_per_thread must be 8 or 14");
   if (t.positions_per_thread < p->n_shape)
     return fail(MPPI_EINVAL, "positions_per_thread must be >= n_shape");
   t.chunk_steps = 0;
@@ -751,8 +733,7 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
     void* base = nullptr;
     CK(cudaGetSymbolAddress(&base, g_static_scratch));
     const int lim = max_smem_optin();
-    const StepFn fns[6] = {step_kernel<0, 8>, step_kernel<0, 14>, step_kernel<0, 16>,
-                           step_kernel<1, 8>, step_kernel<1, 14>, step_kernel<1, 16>};
+    const StepFn fns[4] = {step_u8, step_u14, step_q8, step_q14};
     for (StepFn f : fns) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     g_static_base[dev] = (unsigned char*)base;
   }
@@ -831,7 +812,7 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
   const int sms = num_sms();
   const int S_opts[8] = {2, 4, 7, 10, 14, 20, 27, 32};
   const int NT_opts[3] = {128, 256, 512};
-  const int NP_opts[3] = {8, 14, 16};
+  const int NP_opts[2] = {8, 14};
   const int n = state_dim(p->model);
   double* x0 = new double[(size_t)n * (p->T + 2)];
   for (int d = 0; d < n; ++d) x0[d] = p->x_goal[d];
@@ -888,3 +869,535 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
   if (best_us) *best_us = best_t;
   return MPPI_OK;
 }
+
+// ------------------------------------------------------------------------
+// Batched execution: controllers of mixed model, K, T and obstacle count
+// stepped together by one persistent launch.  Each controller keeps its
+// state in a slot carved from one device pool (admission by memory).  A
+// step packs, in one pinned block, a header, the step table (slot and input
+// offsets of each stepped controller), the work items (controller, tile) in
+// longest-first order and the packed x0 / xref; one host-to-device copy, one
+// persistent kernel whose CTAs pull work items from an atomic counter, one
+// device-to-host copy of the u0.  The sequence is captured in a CUDA graph
+// and replayed while the set of stepped controllers stays the same.
+
+namespace {
+
+struct BatchSlot {
+  bool used = false;
+  mppi_params p;
+  mppi_tiling tl;
+  int n = 3, J = 0, Jcap = 0, smem = 0;
+  size_t off = 0, bytes = 0;   // pool range
+  size_t obst_off = 0;         // pool offset of the obstacle area
+  CtrlDesc D;
+  double tile_cost = 0.0;      // work estimate of one tile
+};
+
+}  // namespace
+
+struct mppi_batch {
+  int max_ctrl = 0;
+  unsigned char* pool = nullptr;
+  size_t pool_bytes = 0;
+  std::vector<std::pair<size_t, size_t>> free_list;  // (offset, size), sorted
+  std::vector<BatchSlot> slots;
+  CtrlDesc* d_descs = nullptr;
+  unsigned char* h_stage = nullptr;
+  unsigned char* d_stage = nullptr;
+  size_t stage_cap = 0;
+  double* h_u0 = nullptr;
+  double* d_u0 = nullptr;
+  int u0_cap = 0;
+  int n_last = 0;
+  cudaStream_t own = nullptr, last = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int> graph_key;  // stepped slots the graph was captured for
+  size_t graph_bytes = 0;
+  int graph_smem = 0, graph_grid = 0;
+  int use_graph = 1;
+  int max_smem = 0;
+};
+
+namespace {
+
+bool pool_alloc(mppi_batch* b, size_t bytes, size_t* off) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  for (size_t i = 0; i < b->free_list.size(); ++i) {
+    auto& f = b->free_list[i];
+    if (f.second >= bytes) {
+      *off = f.first;
+      f.first += bytes;
+      f.second -= bytes;
+      if (f.second == 0) b->free_list.erase(b->free_list.begin() + i);
+      return true;
+    }
+  }
+  return false;
+}
+
+void pool_free(mppi_batch* b, size_t off, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  b->free_list.push_back({off, bytes});
+  std::sort(b->free_list.begin(), b->free_list.end());
+  std::vector<std::pair<size_t, size_t>> merged;
+  for (auto& f : b->free_list) {
+    if (!merged.empty() && merged.back().first + merged.back().second == f.first)
+      merged.back().second += f.second;
+    else
+      merged.push_back(f);
+  }
+  b->free_list.swap(merged);
+}
+
+void drop_graph(mppi_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->graph_key.clear();
+}
+
+// Device bytes of one slot (laid out in this order by slot_layout).
+size_t slot_bytes(const mppi_params* p, const mppi_tiling* t, int Jcap) {
+  const int T = p->T, K = p->K;
+  const int nTiles = (K + t->samples_per_cta - 1) / t->samples_per_cta;
+  int GT = (nTiles + 63) / 64;
+  if (GT < 32) GT = 32;
+  const int nGroups = (nTiles + GT - 1) / GT;
+  size_t off = 0;
+  carve(&off, sizeof(double) * 2 * T);
+  carve(&off, sizeof(float2) * T);
+  carve(&off, sizeof(float2) * T);
+  carve(&off, sizeof(float) * T);
+  carve(&off, sizeof(DevState));
+  carve(&off, sizeof(float) * (size_t)nTiles * 2 * T);
+  carve(&off, sizeof(float4) * nTiles);
+  carve(&off, sizeof(float) * (size_t)nGroups * 2 * T);
+  carve(&off, sizeof(float4) * nGroups);
+  carve(&off, sizeof(unsigned) * (nGroups + 1));
+  carve(&off, sizeof(double) * K);
+  carve(&off, (size_t)K);
+  carve(&off, sizeof(double) * 2 * T);
+  carve(&off, (size_t)align_up(24 * (Jcap > 0 ? Jcap : 1), 16));
+  return off;
+}
+
+void slot_layout(mppi_batch* b, BatchSlot& s, mppi_ctx* c) {
+  const mppi_params* p = &s.p;
+  const int T = p->T, K = p->K;
+  const int nTiles = (K + s.tl.samples_per_cta - 1) / s.tl.samples_per_cta;
+  int GT = (nTiles + 63) / 64;
+  if (GT < 32) GT = 32;
+  const int nGroups = (nTiles + GT - 1) / GT;
+  unsigned char* base = b->pool + s.off;
+  size_t off = 0;
+  c->d_U = (double*)(base + carve(&off, sizeof(double) * 2 * T));
+  c->d_cU = (float2*)(base + carve(&off, sizeof(float2) * T));
+  c->d_cA = (float2*)(base + carve(&off, sizeof(float2) * T));
+  c->d_cw = (float*)(base + carve(&off, sizeof(float) * T));
+  c->d_st = (DevState*)(base + carve(&off, sizeof(DevState)));
+  c->d_part = (float*)(base + carve(&off, sizeof(float) * (size_t)nTiles * 2 * T));
+  c->d_part_rz = (float4*)(base + carve(&off, sizeof(float4) * nTiles));
+  c->d_gpart = (float*)(base + carve(&off, sizeof(float) * (size_t)nGroups * 2 * T));
+  c->d_gpart_rz = (float4*)(base + carve(&off, sizeof(float4) * nGroups));
+  c->d_cnt = (unsigned*)(base + carve(&off, sizeof(unsigned) * (nGroups + 1)));
+  c->d_costs = (double*)(base + carve(&off, sizeof(double) * K));
+  c->d_coll = (uint8_t*)(base + carve(&off, (size_t)K));
+  c->d_Ustar = (double*)(base + carve(&off, sizeof(double) * 2 * T));
+  s.obst_off = s.off + carve(&off, (size_t)align_up(24 * (s.Jcap > 0 ? s.Jcap : 1), 16));
+  c->d_obst = (double*)(b->pool + s.obst_off);
+  c->d_in = nullptr;
+}
+
+int batch_max_smem(mppi_batch* b) {
+  if (b->max_smem == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    size_t stat = 0;
+    if (cudaFuncGetAttributes(&fa, batch_kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+    else cudaGetLastError();
+    b->max_smem = v - align_up((int)stat + 64, 128);
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b->max_smem);
+  }
+  return b->max_smem;
+}
+
+// Fill slot s's descriptor (device pointers into the pool) and upload it.
+int batch_write_desc(mppi_batch* b, int slot) {
+  BatchSlot& s = b->slots[slot];
+  mppi_ctx c;
+  c.p = s.p;
+  c.n = s.n;
+  c.tl = s.tl;
+  slot_layout(b, s, &c);
+  fill_desc(&c);
+  c.D.J = s.J;
+  s.D = c.D;
+  CK(cudaMemcpy(b->d_descs + slot, &s.D, sizeof(CtrlDesc), cudaMemcpyHostToDevice));
+  return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mppi_batch_create(int32_t max_ctrl, size_t pool_bytes, mppi_batch** out) {
+  if (!out) return fail(MPPI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_ctrl < 1 || max_ctrl > (1 << 20)) return fail(MPPI_EINVAL, "max_ctrl out of range");
+  if (pool_bytes < (1u << 20)) return fail(MPPI_EINVAL, "pool must be at least 1 MiB");
+  mppi_batch* b = new (std::nothrow) mppi_batch();
+  if (!b) return fail(MPPI_ENOMEM, "host allocation failed");
+  b->max_ctrl = max_ctrl;
+  b->slots.resize(max_ctrl);
+  if (cudaMalloc((void**)&b->pool, pool_bytes) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_descs, sizeof(CtrlDesc) * max_ctrl) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->pool);
+    cudaFree(b->d_descs);
+    delete b;
+    return fail(MPPI_ENOMEM, "device allocation of the batch pool failed");
+  }
+  b->pool_bytes = pool_bytes;
+  b->free_list.push_back({0, pool_bytes});
+  b->last = b->own;
+  batch_max_smem(b);
+  *out = b;
+  return MPPI_OK;
+}
+
+int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
+                   const mppi_tiling* tiling, const double* cxcyr, int32_t J, int32_t* slot_out) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (!slot_out) return fail(MPPI_EINVAL, "slot is NULL");
+  int rc = validate(p);
+  if (rc) return rc;
+  if (u_init && !finite_all(u_init, 2 * p->T)) return fail(MPPI_EINVAL, "non-finite u_init");
+  if (J < 0 || J > MPPI_MAX_OBSTACLES)
+    return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
+  if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
+  for (int j = 0; j < J; ++j) {
+    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
+    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+  }
+  int slot = -1;
+  for (int i = 0; i < b->max_ctrl; ++i)
+    if (!b->slots[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return fail(MPPI_ENOMEM, "all %d slots are in use", b->max_ctrl);
+  BatchSlot& s = b->slots[slot];
+  s = BatchSlot();
+  s.p = *p;
+  s.n = state_dim(p->model);
+  mppi_tiling req = {0, kBatchThreads, 0, 0};
+  if (tiling) {
+    req = *tiling;
+    req.threads = kBatchThreads;
+  }
+  if (req.samples_per_cta <= 0) req.samples_per_cta = p->K >= 32 ? 32 : p->K;
+  int smem = 0;
+  rc = choose_tiling(p, &req, J, &s.tl, &smem);
+  if (rc) return rc;
+  if (smem > batch_max_smem(b)) return fail(MPPI_EINVAL, "controller too large for the batch kernel");
+  s.J = J;
+  s.Jcap = J;
+  s.bytes = slot_bytes(p, &s.tl, s.Jcap);
+  if (!pool_alloc(b, s.bytes, &s.off))
+    return fail(MPPI_ENOMEM, "admission refused: the slot needs %zu bytes of the batch pool",
+                s.bytes);
+  s.used = true;
+  s.smem = smem;
+  rc = batch_write_desc(b, slot);
+  if (rc) {
+    pool_free(b, s.off, s.bytes);
+    s.used = false;
+    return rc;
+  }
+  DevState st;
+  memset(&st, 0, sizeof(st));
+  st.S_e = p->mu_coarse > 0 ? p->mu_coarse : 1.0;
+  st.first = 1;
+  std::vector<double> U(2 * p->T, 0.0);
+  if (u_init) memcpy(U.data(), u_init, sizeof(double) * 2 * p->T);
+  const int nGroups = s.D.nGroups;
+  bool up = cudaMemcpy(s.D.U, U.data(), sizeof(double) * 2 * p->T, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(s.D.st, &st, sizeof(DevState), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemset(s.D.counters, 0, sizeof(unsigned) * (nGroups + 1)) == cudaSuccess;
+  if (up && J > 0)
+    up = cudaMemset(b->pool + s.obst_off, 0, (size_t)align_up(24 * J, 16)) == cudaSuccess &&
+         cudaMemcpy(b->pool + s.obst_off, cxcyr, sizeof(double) * 3 * J, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!up) {
+    pool_free(b, s.off, s.bytes);
+    s.used = false;
+    return fail(MPPI_ECUDA, "slot initialisation failed");
+  }
+  prep_kernel<<<1, 256, 0, b->own>>>(s.D, 1);
+  if (cudaStreamSynchronize(b->own) != cudaSuccess) {
+    pool_free(b, s.off, s.bytes);
+    s.used = false;
+    return fail(MPPI_ECUDA, "slot prep failed");
+  }
+  s.tile_cost = (double)s.tl.samples_per_cta * p->T * (8.0 * p->n_shape * (J > 0 ? J : 1) + 135.0);
+  drop_graph(b);
+  *slot_out = slot;
+  return MPPI_OK;
+}
+
+int mppi_batch_set_obstacles(mppi_batch* b, int32_t slot, const double* cxcyr, int32_t J) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (slot < 0 || slot >= b->max_ctrl || !b->slots[slot].used)
+    return fail(MPPI_EINVAL, "slot %d is not in use", slot);
+  if (J < 0 || J > MPPI_MAX_OBSTACLES)
+    return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
+  if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
+  for (int j = 0; j < J; ++j) {
+    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
+    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+  }
+  BatchSlot& s = b->slots[slot];
+  mppi_tiling t;
+  int smem = 0;
+  int rc = choose_tiling(&s.p, &s.tl, J, &t, &smem);
+  if (rc) return rc;
+  if (smem > batch_max_smem(b)) return fail(MPPI_EINVAL, "obstacle set too large");
+  CK(cudaStreamSynchronize(b->last));
+  if (J > s.Jcap) {
+    // grow the slot: a new range holding the state and the larger obstacle area
+    const size_t nbytes = slot_bytes(&s.p, &s.tl, J);
+    size_t noff = 0;
+    if (!pool_alloc(b, nbytes, &noff))
+      return fail(MPPI_ENOMEM, "admission refused: %zu bytes for the obstacle set", nbytes);
+    CK(cudaMemcpy(b->pool + noff, b->pool + s.off, s.bytes, cudaMemcpyDeviceToDevice));
+    pool_free(b, s.off, s.bytes);
+    s.off = noff;
+    s.bytes = nbytes;
+    s.Jcap = J;
+  }
+  s.J = J;
+  s.smem = smem;
+  rc = batch_write_desc(b, slot);
+  if (rc) return rc;
+  if (J > 0) {
+    CK(cudaMemset(b->pool + s.obst_off, 0, (size_t)align_up(24 * J, 16)));
+    CK(cudaMemcpy(b->pool + s.obst_off, cxcyr, sizeof(double) * 3 * J, cudaMemcpyHostToDevice));
+  }
+  s.tile_cost = (double)s.tl.samples_per_cta * s.p.T * (8.0 * s.p.n_shape * (J > 0 ? J : 1) + 135.0);
+  drop_graph(b);
+  return MPPI_OK;
+}
+
+int mppi_batch_remove(mppi_batch* b, int32_t slot) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (slot < 0 || slot >= b->max_ctrl || !b->slots[slot].used)
+    return fail(MPPI_EINVAL, "slot %d is not in use", slot);
+  CK(cudaStreamSynchronize(b->last));
+  BatchSlot& s = b->slots[slot];
+  pool_free(b, s.off, s.bytes);
+  s.used = false;
+  drop_graph(b);
+  return MPPI_OK;
+}
+
+int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double* x0s,
+                    const double* const* xrefs, void* stream) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (n < 0 || (n > 0 && (!slots || !x0s))) return fail(MPPI_EINVAL, "bad slot list");
+  cudaStream_t st = stream ? (cudaStream_t)stream : b->own;
+  if (n == 0) return MPPI_OK;
+  // validate, compute sizes
+  size_t n_items = 0, n_in = 0;
+  int smem = 0;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) {
+    const int sl = slots[i];
+    if (sl < 0 || sl >= b->max_ctrl || !b->slots[sl].used)
+      return fail(MPPI_EINVAL, "slot %d is not in use", sl);
+    for (int k = 0; k < i; ++k)
+      if (slots[k] == sl) return fail(MPPI_EINVAL, "slot %d listed twice", sl);
+    const BatchSlot& s = b->slots[sl];
+    n_items += s.D.nTiles;
+    n_in += (size_t)s.n * (s.p.T + 2);
+    smem = std::max(smem, s.smem);
+    order[i] = i;
+  }
+  const size_t head = sizeof(BatchHdr) + sizeof(StepEntry) * n + sizeof(WorkItem) * n_items;
+  const size_t inputs_off = (head + 15) & ~(size_t)15;
+  const size_t bytes = inputs_off + sizeof(double) * n_in;
+  // staging buffers
+  if (b->last) CK(cudaStreamSynchronize(b->last));
+  if (bytes > b->stage_cap) {
+    drop_graph(b);
+    cudaFreeHost(b->h_stage);
+    cudaFree(b->d_stage);
+    b->h_stage = nullptr;
+    b->d_stage = nullptr;
+    size_t cap = std::max(bytes, (size_t)1 << 16) * 2;
+    if (cudaMallocHost((void**)&b->h_stage, cap) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_stage, cap) != cudaSuccess) {
+      cudaGetLastError();
+      b->stage_cap = 0;
+      return fail(MPPI_ENOMEM, "staging allocation failed");
+    }
+    b->stage_cap = cap;
+  }
+  if (n > b->u0_cap) {
+    drop_graph(b);
+    cudaFreeHost(b->h_u0);
+    cudaFree(b->d_u0);
+    int cap = std::max(n, 64) * 2;
+    if (cudaMallocHost((void**)&b->h_u0, sizeof(double) * 2 * cap) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_u0, sizeof(double) * 2 * cap) != cudaSuccess) {
+      cudaGetLastError();
+      b->u0_cap = 0;
+      return fail(MPPI_ENOMEM, "output allocation failed");
+    }
+    b->u0_cap = cap;
+  }
+  // pack: header, step table, longest-first work items, inputs
+  BatchHdr* hdr = (BatchHdr*)b->h_stage;
+  StepEntry* steps = (StepEntry*)(b->h_stage + sizeof(BatchHdr));
+  WorkItem* items = (WorkItem*)(steps + n);
+  double* in = (double*)(b->h_stage + inputs_off);
+  std::sort(order.begin(), order.end(), [&](int a, int c) {
+    return b->slots[slots[a]].tile_cost > b->slots[slots[c]].tile_cost;
+  });
+  size_t w = 0, d = 0;
+  for (int i = 0; i < n; ++i) {
+    const BatchSlot& s = b->slots[slots[i]];
+    const int nn = s.n, T = s.p.T;
+    const double* x0 = x0s + (size_t)i * 6;
+    if (!finite_all(x0, nn)) return fail(MPPI_EINVAL, "x0 of slot %d is not finite", slots[i]);
+    steps[i].slot = slots[i];
+    steps[i].x0_off = (int)d;
+    memcpy(in + d, x0, sizeof(double) * nn);
+    d += nn;
+    steps[i].xref_off = (int)d;
+    const double* xr = xrefs ? xrefs[i] : nullptr;
+    if (xr && !finite_all(xr, (T + 1) * nn)) return fail(MPPI_EINVAL, "xref of slot %d is not finite", slots[i]);
+    for (int t = 0; t <= T; ++t)
+      for (int k = 0; k < nn; ++k) in[d + t * nn + k] = xr ? xr[t * nn + k] : s.p.x_goal[k];
+    d += (size_t)(T + 1) * nn;
+  }
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = order[oi];
+    const BatchSlot& s = b->slots[slots[i]];
+    for (int t = 0; t < s.D.nTiles; ++t) items[w++] = WorkItem{i, t};
+  }
+  hdr->n_steps = n;
+  hdr->n_items = (int)n_items;
+  hdr->next = 0u;
+  hdr->inputs_off = (int)inputs_off;
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, smem));
+  if (occ < 1) return fail(MPPI_EINVAL, "batch needs %d bytes of shared memory per CTA", smem);
+  const int grid = (int)std::min<size_t>((size_t)num_sms() * occ, n_items);
+  std::vector<int> key(slots, slots + n);
+  const bool same = b->use_graph && b->gexec && key == b->graph_key && bytes == b->graph_bytes &&
+                    smem == b->graph_smem && grid == b->graph_grid && st == b->last;
+  if (same) {
+    CK(cudaGraphLaunch(b->gexec, st));
+  } else {
+    drop_graph(b);
+    bool capture = b->use_graph != 0;
+    if (capture) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(b->d_stage, b->h_stage, bytes, cudaMemcpyHostToDevice, st);
+    batch_kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, b->d_stage, b->d_u0);
+    cudaMemcpyAsync(b->h_u0, b->d_u0, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st);
+    if (capture) {
+      CK(cudaStreamEndCapture(st, &b->graph));
+      CK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+      b->graph_key = key;
+      b->graph_bytes = bytes;
+      b->graph_smem = smem;
+      b->graph_grid = grid;
+      CK(cudaGraphLaunch(b->gexec, st));
+    } else {
+      CK(cudaGetLastError());
+    }
+  }
+  b->last = st;
+  b->n_last = n;
+  return MPPI_OK;
+}
+
+int mppi_batch_get_controls(mppi_batch* b, double* u0s, int32_t n) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (n != b->n_last) return fail(MPPI_EINVAL, "n=%d but the last step had %d controllers", n, b->n_last);
+  CK(cudaStreamSynchronize(b->last));
+  if (u0s && n > 0) memcpy(u0s, b->h_u0, sizeof(double) * 2 * n);
+  return MPPI_OK;
+}
+
+int mppi_batch_get_state(mppi_batch* b, int32_t slot, double* U, double* costs, double* scalars) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (slot < 0 || slot >= b->max_ctrl || !b->slots[slot].used)
+    return fail(MPPI_EINVAL, "slot %d is not in use", slot);
+  CK(cudaStreamSynchronize(b->last));
+  const BatchSlot& s = b->slots[slot];
+  if (U) CK(cudaMemcpy(U, s.D.U, sizeof(double) * 2 * s.p.T, cudaMemcpyDeviceToHost));
+  if (costs) CK(cudaMemcpy(costs, s.D.costs, sizeof(double) * s.p.K, cudaMemcpyDeviceToHost));
+  if (scalars) {
+    DevState st;
+    CK(cudaMemcpy(&st, s.D.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    scalars[0] = st.rho;
+    scalars[1] = st.Z;
+    scalars[2] = st.CB_star;
+    scalars[3] = st.S_e;
+    scalars[4] = st.beta_used;
+    scalars[5] = st.beta_d;
+    scalars[6] = st.S_e_used;
+    scalars[7] = (double)st.iter;
+    if (st.status == kStatusTimeout)
+      return fail(MPPI_ETIMEOUT, "a bounded device wait (obstacle staging) expired");
+  }
+  return MPPI_OK;
+}
+
+int mppi_batch_info(mppi_batch* b, int32_t slot, mppi_tiling* t, uint64_t* bytes,
+                    uint64_t* pool_free_bytes) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (slot >= 0) {
+    if (slot >= b->max_ctrl || !b->slots[slot].used)
+      return fail(MPPI_EINVAL, "slot %d is not in use", slot);
+    if (t) *t = b->slots[slot].tl;
+    if (bytes) *bytes = b->slots[slot].bytes;
+  }
+  if (pool_free_bytes) {
+    size_t f = 0;
+    for (auto& e : b->free_list) f += e.second;
+    *pool_free_bytes = f;
+  }
+  return MPPI_OK;
+}
+
+int mppi_batch_set_graph(mppi_batch* b, int32_t enable) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (b->last) CK(cudaStreamSynchronize(b->last));
+  drop_graph(b);
+  b->use_graph = enable ? 1 : 0;
+  return MPPI_OK;
+}
+
+int mppi_batch_destroy(mppi_batch* b) {
+  if (!b) return MPPI_OK;
+  if (b->last) cudaStreamSynchronize(b->last);
+  drop_graph(b);
+  cudaFree(b->pool);
+  cudaFree(b->d_descs);
+  cudaFreeHost(b->h_stage);
+  cudaFree(b->d_stage);
+  cudaFreeHost(b->h_u0);
+  cudaFree(b->d_u0);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+  return MPPI_OK;
+}
+
+}  // extern "C"

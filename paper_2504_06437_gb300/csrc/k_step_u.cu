@@ -1,0 +1,18 @@
+// One-controller step kernels of the unicycle model.
+#include "kernels.cuh"
+
+namespace dbm {
+
+__global__ void __launch_bounds__(512) step_u8(const __grid_constant__ CtrlDesc D,
+                                                const double* __restrict__ x0,
+                                                const double* __restrict__ xref) {
+  step_body<0, 8>(D, x0, xref);
+}
+
+__global__ void __launch_bounds__(512) step_u14(const __grid_constant__ CtrlDesc D,
+                                                 const double* __restrict__ x0,
+                                                 const double* __restrict__ xref) {
+  step_body<0, 14>(D, x0, xref);
+}
+
+}  // namespace dbm

@@ -1,0 +1,53 @@
+// Kernels of the DBaS-Log-MPPI library, defined in separate translation
+// units (compiled in parallel) and launched from the host code in
+// dbasmppi.cu.
+#pragma once
+
+#include "mppi_tile.cuh"
+
+namespace dbm {
+
+// One step of one controller: one CTA per tile (MODEL: 0 unicycle,
+// 1 planar quadrotor; 8 or 14 world points per barrier thread).
+__global__ void step_u8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                        const double* __restrict__ xref);
+__global__ void step_u14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                         const double* __restrict__ xref);
+__global__ void step_q8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                        const double* __restrict__ xref);
+__global__ void step_q14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                         const double* __restrict__ xref);
+
+// Batched step: persistent CTAs pull (controller, tile) work items.
+struct WorkItem {
+  int ctrl;  // index into the step table
+  int tile;
+};
+struct StepEntry {
+  int slot;
+  int x0_off;  // offsets, in doubles, into the packed inputs
+  int xref_off;
+  int pad;
+};
+struct BatchHdr {
+  int n_steps, n_items;
+  unsigned next;
+  int inputs_off;  // byte offset of the packed inputs
+};
+constexpr int kBatchThreads = 256;
+__global__ void batch_kernel(const CtrlDesc* __restrict__ descs, unsigned char* stage,
+                             double* __restrict__ u0_out);
+
+// Body of the one-controller step kernels.
+template <int MODEL, int NPOS>
+__device__ __forceinline__ void step_body(const CtrlDesc& D, const double* __restrict__ x0,
+                                          const double* __restrict__ xref) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ TileScratch ts;
+  if (threadIdx.x == 0) mbar_init(&ts.mbar);
+  __syncthreads();
+  uint32_t phase = 0u;
+  run_tile<MODEL, NPOS>(D, blockIdx.x, x0, xref, smem, ts, phase);
+}
+
+}  // namespace dbm

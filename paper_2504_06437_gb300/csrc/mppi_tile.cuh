@@ -197,7 +197,8 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // (Eq. 4), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"),
 // S_e (Eq. 10, C_B floored at 0 inside the logarithm), shift, state update.
 template <int MODEL, int NPOS>
-__device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts) {
+__device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
+                            double* u0_out) {
   const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31;
   const int T = D.T, P = D.P;
   double* Us = reinterpret_cast<double*>(smem + L.Us);
@@ -253,6 +254,10 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       st->S_e_used = S_e_used;
       st->u0[0] = Us[0];
       st->u0[1] = Us[1];
+      if (u0_out) {
+        u0_out[0] = Us[0];
+        u0_out[1] = Us[1];
+      }
       st->S_e = S_e_next;
       st->beta = ts.beta0;
       st->first = 0;
@@ -273,9 +278,9 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 // One tile of one controller.  ts.mbar must be initialised; mbar_phase is
 // each thread's own copy of the parity of the barrier's next completion.
 template <int MODEL, int NPOS>
-__device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
+__device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
                          const double* __restrict__ xrefg, char* smem, TileScratch& ts,
-                         uint32_t& mbar_phase) {
+                         uint32_t& mbar_phase, double* u0_out = nullptr) {
   constexpr int n = Dyn<MODEL>::n;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
@@ -511,7 +516,7 @@ __device__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__
   merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z, col_hi,
                  col_lo, mbuf, tid, nthreads);
   if (tid == 0) D.counters[D.nGroups] = 0u;
-  final_stage<MODEL, NPOS>(D, smem, L, ts);
+  final_stage<MODEL, NPOS>(D, smem, L, ts, u0_out);
 }
 
 }  // namespace dbm

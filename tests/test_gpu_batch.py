@@ -1,0 +1,129 @@
+"""Batched execution on the GPU: each controller stepped inside the batch
+gives, bit for bit, what it gives alone through the context API with the
+same launch shape; graph replay equals eager launches; admission by memory;
+and batch results agree with the CPU oracle."""
+import numpy as np
+import pytest
+
+from paper_2504_06437_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06437_gb300 import binding
+    binding.build()
+    binding.load()
+    return binding
+
+
+def mix(n, seed=0, K_hi=3000):
+    g = W.rng(seed)
+    return [W._mixed_world(g, i, seed, 64, K_hi, 10, 40, 0 if i == 3 else 5, 80) for i in range(n)]
+
+
+def test_batch_equals_alone_bitwise(gpu):
+    worlds = mix(6)
+    with gpu.Batch(16, 256 << 20) as b:
+        slots = [b.add(w.params, w.obstacles) for w in worlds]
+        shapes = [b.slot_info(s) for s in slots]
+        for step in range(2):
+            x0s = [w.x_start for w in worlds]
+            xrefs = [w.reference(w.x_start) for w in worlds]
+            b.step(slots, x0s, xrefs)
+            u_b = b.controls()
+            st_b = [b.state(s) for s in slots]
+            if step == 0:
+                alone = []
+                for w, sh in zip(worlds, shapes):
+                    g = gpu.Controller(w.params, tiling=dict(samples_per_cta=sh["samples_per_cta"],
+                                                             threads=256,
+                                                             positions_per_thread=sh["positions_per_thread"]))
+                    g.set_obstacles(w.obstacles)
+                    alone.append(g)
+            for i, (w, g) in enumerate(zip(worlds, alone)):
+                g.step(w.x_start, w.reference(w.x_start))
+                u0, U = g.get_control(want_U=True)
+                d = g.get_debug()
+                np.testing.assert_array_equal(u_b[i], u0)
+                np.testing.assert_array_equal(st_b[i]["U"], U)
+                np.testing.assert_array_equal(st_b[i]["costs"], d["costs"])
+                assert st_b[i]["S_e"] == d["S_e_next"]
+        for g in alone:
+            g.close()
+
+
+def test_graph_replay_equals_eager(gpu):
+    worlds = mix(5, seed=2)
+    outs = []
+    for use_graph in (True, False):
+        with gpu.Batch(8, 256 << 20) as b:
+            b.set_graph(use_graph)
+            slots = [b.add(w.params, w.obstacles) for w in worlds]
+            us = []
+            for _ in range(3):
+                b.step(slots, [w.x_start for w in worlds], [w.reference(w.x_start) for w in worlds])
+                us.append(b.controls())
+            outs.append(np.array(us))
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_subsets_and_order(gpu):
+    """Stepping a subset, in another order, leaves the others untouched and
+    gives the same per-controller results."""
+    worlds = mix(4, seed=3)
+    with gpu.Batch(8, 256 << 20) as b, gpu.Batch(8, 256 << 20) as c:
+        sb = [b.add(w.params, w.obstacles) for w in worlds]
+        sc = [c.add(w.params, w.obstacles) for w in worlds]
+        b.step(sb, [w.x_start for w in worlds], [w.reference(w.x_start) for w in worlds])
+        ub = b.controls()
+        order = [2, 0, 3]
+        c.step([sc[i] for i in order], [worlds[i].x_start for i in order],
+               [worlds[i].reference(worlds[i].x_start) for i in order])
+        uc = c.controls()
+        for j, i in enumerate(order):
+            np.testing.assert_array_equal(uc[j], ub[i])
+        assert c.state(sc[1])["iter"] == 0
+
+
+def test_admission_by_memory(gpu):
+    w = W.quad2d(0, K=8192, T=60)
+    with gpu.Batch(64, 4 << 20) as b:
+        slots = []
+        with pytest.raises(gpu.MppiError) as e:
+            for _ in range(64):
+                slots.append(b.add(w.params, w.obstacles))
+        assert e.value.code == gpu.MPPI_ENOMEM
+        assert len(slots) >= 1
+        free_before = b.slot_info()["pool_free"]
+        b.remove(slots[0])
+        assert b.slot_info()["pool_free"] > free_before
+        slots[0] = b.add(w.params, w.obstacles)          # fits again
+        b.step(slots, [w.x_start] * len(slots))
+        assert np.all(np.isfinite(b.controls()))
+
+
+def test_batch_matches_oracle(gpu, orc):
+    worlds = [W.unicycle_small(1), W.quad2d(1, K=700, T=30)]
+    with gpu.Batch(4, 128 << 20) as b:
+        slots = [b.add(w.params, w.obstacles) for w in worlds]
+        for step in range(2):
+            ctls = [orc.new_controller(w.params) for w in worlds] if step == 0 else ctls
+            if step > 0:
+                # identical inputs for the second step: resynchronise is not
+                # possible in the batch API, so only the first step is compared
+                break
+            xrefs = [w.reference(w.x_start) for w in worlds]
+            b.step(slots, [w.x_start for w in worlds], xrefs)
+            u = b.controls()
+            for i, (w, s) in enumerate(zip(worlds, slots)):
+                ro = orc.step(w.params, w.obstacles, w.x_start, xrefs[i], ctls[i])
+                st = b.state(s)
+                rel = np.abs(st["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
+                assert rel.max() <= 1e-4
+                np.testing.assert_allclose(u[i], ro["u0"], rtol=0, atol=1e-5)
+                np.testing.assert_allclose(st["U"], ro["U_next"], rtol=0, atol=1e-5)

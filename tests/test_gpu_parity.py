@@ -133,7 +133,7 @@ def test_quad_ragged_tiles(gpu, orc):
 
 @pytest.mark.parametrize("tiling", [
     dict(samples_per_cta=32, threads=64, positions_per_thread=8, chunk_steps=0),
-    dict(samples_per_cta=7, threads=512, positions_per_thread=16, chunk_steps=3),
+    dict(samples_per_cta=7, threads=512, positions_per_thread=14, chunk_steps=3),
     dict(samples_per_cta=1, threads=128, positions_per_thread=14, chunk_steps=0),
     dict(samples_per_cta=20, threads=256, positions_per_thread=8, chunk_steps=11),
 ])
