@@ -326,6 +326,117 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, ws, rank, local):
+    """Serving workload: robots of mixed model, K, T and obstacle count send
+    closed-loop control-step requests to the continuous-batching runtime.
+    First the capacity is measured with every robot resubmitting at once
+    (saturation), then requests arrive with exponential think times sized to
+    a fraction of that capacity; latency is submission to completion.  The
+    plain form serves the same requests one at a time through the context
+    API (mppi_step + mppi_get_control)."""
+    import heapq
+
+    import torch
+    from paper_2504_06437_gb300 import binding, workloads as W
+
+    torch.cuda.set_device(local)
+    binding.load()
+    worlds = W.serving_mix(args.robots, seed=rank)
+    g = np.random.default_rng(rank)
+    srv = binding.Server(len(worlds), args.pool_mb << 20, lanes=args.lanes)
+    work_of = {}
+
+    def run(n_req_per_robot, think_mean):
+        waiting = list(range(len(worlds)))   # admission queue (memory)
+        active, x, done, lat = {}, {}, {}, []
+        timers = []
+        t_start = time.perf_counter()
+        completed = 0
+        total_work = 0
+        while waiting or active:
+            while waiting:
+                i = waiting[0]
+                r = srv.join(worlds[i].params, worlds[i].obstacles)
+                if r is None:
+                    break
+                waiting.pop(0)
+                active[r] = i
+                x[r] = worlds[i].x_start.copy()
+                done[r] = 0
+                heapq.heappush(timers, (time.perf_counter() + g.exponential(think_mean) if think_mean else 0.0, r))
+            now = time.perf_counter()
+            while timers and timers[0][0] <= now:
+                _, r = heapq.heappop(timers)
+                w = worlds[active[r]]
+                srv.submit(r, x[r], w.reference(x[r]))
+            for (r, u0, x1, l, st) in srv.poll():
+                w = worlds[active[r]]
+                lat.append(l)
+                completed += 1
+                total_work += int(w.params["K"]) * int(w.params["T"])
+                done[r] += 1
+                x[r] = x1[: w.n].copy()
+                if done[r] >= n_req_per_robot:
+                    srv.leave(r)
+                    del active[r]
+                else:
+                    heapq.heappush(timers, (time.perf_counter() + (g.exponential(think_mean) if think_mean else 0.0), r))
+        el = time.perf_counter() - t_start
+        return dict(seconds=el, requests=completed, work=total_work, lat=np.array(lat))
+
+    run(1, 0.0)  # warm-up
+    st0 = srv.stats()
+    cap = run(args.serve_steps, 0.0)
+    st1 = srv.stats()
+    cap_rps = cap["requests"] / cap["seconds"]
+    think = len(worlds) / (args.load * cap_rps)
+    loaded = run(args.serve_steps, think)
+    st2 = srv.stats()
+    srv.close()
+    # plain: the same kind of requests served one at a time
+    plain_lat, plain_work = [], 0
+    n_plain = min(len(worlds), args.plain_robots)
+    t0 = time.perf_counter()
+    for w in worlds[:n_plain]:
+        with binding.Controller(w.params) as c:
+            c.set_obstacles(w.obstacles)
+            xx = w.x_start
+            for _ in range(args.plain_steps):
+                a = time.perf_counter()
+                c.step(xx, w.reference(xx))
+                c.get_control()
+                plain_lat.append(time.perf_counter() - a)
+                plain_work += int(w.params["K"]) * int(w.params["T"])
+    plain_s = float(np.sum(plain_lat))
+    if rank != 0:
+        return
+    pct = lambda a, q: 1e3 * float(np.percentile(a, q))
+    line = {"metric": METRIC + " and p50/p99 step latency (serving)",
+            "value": loaded["work"] / loaded["seconds"], "unit": UNIT, "n_gpus": ws,
+            "steps": loaded["requests"], "warmup": len(worlds),
+            "ms_per_step": 1e3 * loaded["seconds"] / max(1, loaded["requests"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving_mix: {len(worlds)} robots, half unicycle half planar quadrotor, "
+                                   "K log-uniform 512..32768, T 20..100, 5..500 obstacles",
+                       "requests_per_robot": args.serve_steps, "lanes": args.lanes,
+                       "pool_mb": args.pool_mb, "offered_load": f"{args.load:.2f} of measured capacity",
+                       "arrivals": "closed loop, exponential think time after each reply"},
+            "latency_ms": {"p50": pct(loaded["lat"], 50), "p99": pct(loaded["lat"], 99)},
+            "capacity": {"value": cap["work"] / cap["seconds"], "unit": UNIT,
+                         "requests_per_s": cap_rps,
+                         "latency_ms": {"p50": pct(cap["lat"], 50), "p99": pct(cap["lat"], 99)},
+                         "mean_batch": (st1["requests"] - st0["requests"]) / max(1, st1["batches"] - st0["batches"])},
+            "loaded": {"requests_per_s": loaded["requests"] / loaded["seconds"],
+                       "mean_batch": (st2["requests"] - st1["requests"]) / max(1, st2["batches"] - st1["batches"])},
+            "plain": {"value": plain_work / plain_s, "unit": UNIT,
+                      "form": "one request at a time: mppi_step + mppi_get_control",
+                      "requests": len(plain_lat),
+                      "latency_ms": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99)}},
+            "serving_over_plain": (cap["work"] / cap["seconds"]) / (plain_work / plain_s)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,6 +449,13 @@ def main():
     ap.add_argument("--ref-samples", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--robots", type=int, default=1000)
+    ap.add_argument("--serve-steps", type=int, default=10)
+    ap.add_argument("--lanes", type=int, default=2)
+    ap.add_argument("--pool-mb", type=int, default=2048)
+    ap.add_argument("--load", type=float, default=0.5)
+    ap.add_argument("--plain-robots", type=int, default=100)
+    ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default launch shape instead of the autotuned one")
     args = ap.parse_args()
@@ -349,6 +467,9 @@ def main():
         return
     if args.workload == "batch_mix":
         run_batch(args, ws, rank, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, ws, rank, local)
         return
 
     import torch

@@ -263,6 +263,50 @@ int mppi_batch_set_graph(mppi_batch* b, int32_t enable);
 /* Release the batch and its pool.  NULL is a no-op. */
 int mppi_batch_destroy(mppi_batch* b);
 
+/* ---- Serving runtime: continuous batching of control-step requests from
+ * many robots.  Robots join by taking a slot of a device pool (admission by
+ * memory) and keep their warm-start sequence, generator counter, exploration
+ * rate and barrier state on the device.  A scheduler thread keeps up to
+ * `lanes` batched steps in flight, each on its own stream; when a lane is
+ * free it launches one persistent batch holding every queued request, so
+ * requests that arrive while others run are served by the next batch and
+ * the batches overlap on the device.  Each result equals, bit for bit, the
+ * robot's result alone through a context with the same launch shape.  Not
+ * part of the paper. */
+typedef struct mppi_server mppi_server;
+
+int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes,
+                       mppi_server** out);
+
+/* Admit a robot (parameters, initial sequence or NULL, obstacle set).
+ * MPPI_ENOMEM: no free slot or no room in the pool now (retry after others
+ * leave). */
+int mppi_server_join(mppi_server* s, const mppi_params* p, const double* u_init,
+                     const double* cxcyr, int32_t J, int32_t* robot);
+
+/* Release a robot's slot (MPPI_ESTATE if it has a request in flight). */
+int mppi_server_leave(mppi_server* s, int32_t robot);
+
+/* Queue one step request: measured state x0 (n doubles), reference
+ * ((T+1) x n) or NULL (goal repeated); copied.  One request per robot at a
+ * time (MPPI_ESTATE otherwise).  Thread-safe; returns at once. */
+int mppi_server_submit(mppi_server* s, int32_t robot, const double* x0,
+                       const double* xref);
+
+/* Up to max completed requests, oldest first: robot ids, u0 (2 each), the
+ * model-predicted next state (6 each), latency from submission in seconds,
+ * status (MPPI_OK or the error of the launch).  *n receives the count. */
+int mppi_server_poll(mppi_server* s, int32_t max, int32_t* robots, double* u0s,
+                     double* x1s, double* latency_s, int32_t* status, int32_t* n);
+
+/* Counters: batches launched, requests completed, requests queued or in
+ * flight, free pool bytes. */
+int mppi_server_stats(mppi_server* s, uint64_t* batches, uint64_t* requests,
+                      int32_t* pending, uint64_t* pool_free_bytes);
+
+/* Stop the scheduler, wait for work in flight, release everything. */
+int mppi_server_destroy(mppi_server* s);
+
 /* Release everything owned by the context.  NULL is a no-op. */
 int mppi_destroy(mppi_ctx* c);
 

@@ -20,7 +20,7 @@ _DEPS = _SOURCES + ["csrc/mppi_device.cuh", "csrc/mppi_tile.cuh", "csrc/kernels.
 HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC"]
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread"]
 
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE = 0, -1, -2, -3, -4, -5
 UNICYCLE, QUAD2D = 0, 1
@@ -62,8 +62,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(_SOURCES)) as ex:
         list(ex.map(compile_one, range(len(_SOURCES))))
     tmp = _LIB + f".tmp{tag}"
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs],
-                   check=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs,
+                    "-lpthread"], check=True)
     os.replace(tmp, _LIB)
     for o in objs:
         os.remove(o)
@@ -137,6 +137,16 @@ def load():
                                     C.POINTER(C.c_uint64)]
     lib.mppi_batch_set_graph.argtypes = [vp, C.c_int32]
     lib.mppi_batch_destroy.argtypes = [vp]
+    lib.mppi_server_create.argtypes = [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(vp)]
+    lib.mppi_server_join.argtypes = [vp, C.POINTER(Params), _dp, _dp, C.c_int32,
+                                     C.POINTER(C.c_int32)]
+    lib.mppi_server_leave.argtypes = [vp, C.c_int32]
+    lib.mppi_server_submit.argtypes = [vp, C.c_int32, _dp, _dp]
+    lib.mppi_server_poll.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), _dp, _dp, _dp,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.mppi_server_stats.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
+    lib.mppi_server_destroy.argtypes = [vp]
     lib.mppi_last_error.restype = C.c_char_p
     _lib = lib
     return lib
@@ -397,3 +407,76 @@ class Batch:
 
     def set_graph(self, enable: bool):
         _check(load().mppi_batch_set_graph(self.h, int(bool(enable))))
+
+
+class Server:
+    """Continuous-batching serving runtime (mppi_server_*)."""
+
+    def __init__(self, max_robots: int, pool_bytes: int, lanes: int = 2):
+        h = C.c_void_p()
+        _check(load().mppi_server_create(int(max_robots), int(pool_bytes), int(lanes), C.byref(h)))
+        self.h = h
+        self.dims = {}
+        self._buf = 4096
+        self._r = np.zeros(self._buf, dtype=np.int32)
+        self._u = np.zeros((self._buf, 2))
+        self._x = np.zeros((self._buf, 6))
+        self._l = np.zeros(self._buf)
+        self._s = np.zeros(self._buf, dtype=np.int32)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().mppi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def join(self, cfg: dict, obstacles, u_init=None):
+        """Robot id, or None when admission is refused for lack of memory."""
+        p = make_params(cfg)
+        ob = _f64(obstacles).reshape(-1, 3)
+        u = None if u_init is None else _f64(u_init).reshape(int(p.T), 2)
+        r = C.c_int32()
+        rc = load().mppi_server_join(self.h, C.byref(p), _ptr(u) if u is not None else None,
+                                     _ptr(ob) if ob.size else None, ob.shape[0], C.byref(r))
+        if rc == MPPI_ENOMEM:
+            return None
+        _check(rc)
+        self.dims[r.value] = (int(p.T), 6 if p.model == QUAD2D else 3)
+        return r.value
+
+    def leave(self, robot: int):
+        _check(load().mppi_server_leave(self.h, int(robot)))
+        self.dims.pop(robot, None)
+
+    def submit(self, robot: int, x0, xref=None):
+        x0 = _f64(x0)
+        xr = None if xref is None else _f64(xref)
+        _check(load().mppi_server_submit(self.h, int(robot), _ptr(x0),
+                                         _ptr(xr) if xr is not None else None))
+
+    def poll(self):
+        """Completed requests: list of (robot, u0, predicted x1, latency s, status)."""
+        n = C.c_int32()
+        _check(load().mppi_server_poll(self.h, self._buf, self._r.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       _ptr(self._u), _ptr(self._x), _ptr(self._l),
+                                       self._s.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)))
+        k = n.value
+        return [(int(self._r[i]), self._u[i].copy(), self._x[i].copy(), float(self._l[i]),
+                 int(self._s[i])) for i in range(k)]
+
+    def stats(self) -> dict:
+        b, r, f = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        q = C.c_int32()
+        _check(load().mppi_server_stats(self.h, C.byref(b), C.byref(r), C.byref(q), C.byref(f)))
+        return dict(batches=b.value, requests=r.value, pending=q.value, pool_free=f.value)

@@ -6,6 +6,11 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <deque>
+#include <mutex>
+#include <thread>
 #include <new>
 #include <vector>
 
@@ -896,6 +901,25 @@ struct BatchSlot {
 
 }  // namespace
 
+// One launch lane: staging, outputs, stream state and captured graph of
+// one in-flight batched step.  A batch has one lane for mppi_batch_step; the
+// serving runtime keeps several so that steps overlap on the device.
+struct BatchLane {
+  unsigned char* h_stage = nullptr;
+  unsigned char* d_stage = nullptr;
+  size_t stage_cap = 0;
+  double* h_out = nullptr;  // 8 doubles per stepped controller: u0, predicted x1
+  double* d_out = nullptr;
+  int out_cap = 0;
+  int n_last = 0;
+  cudaStream_t last = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int> graph_key;  // stepped slots the graph was captured for
+  size_t graph_bytes = 0;
+  int graph_smem = 0, graph_grid = 0;
+};
+
 struct mppi_batch {
   int max_ctrl = 0;
   unsigned char* pool = nullptr;
@@ -903,19 +927,8 @@ struct mppi_batch {
   std::vector<std::pair<size_t, size_t>> free_list;  // (offset, size), sorted
   std::vector<BatchSlot> slots;
   CtrlDesc* d_descs = nullptr;
-  unsigned char* h_stage = nullptr;
-  unsigned char* d_stage = nullptr;
-  size_t stage_cap = 0;
-  double* h_u0 = nullptr;
-  double* d_u0 = nullptr;
-  int u0_cap = 0;
-  int n_last = 0;
-  cudaStream_t own = nullptr, last = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<int> graph_key;  // stepped slots the graph was captured for
-  size_t graph_bytes = 0;
-  int graph_smem = 0, graph_grid = 0;
+  BatchLane lane;
+  cudaStream_t own = nullptr;
   int use_graph = 1;
   int max_smem = 0;
 };
@@ -951,12 +964,23 @@ void pool_free(mppi_batch* b, size_t off, size_t bytes) {
   b->free_list.swap(merged);
 }
 
-void drop_graph(mppi_batch* b) {
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  b->gexec = nullptr;
-  b->graph = nullptr;
-  b->graph_key.clear();
+void drop_lane_graph(BatchLane& L) {
+  if (L.gexec) cudaGraphExecDestroy(L.gexec);
+  if (L.graph) cudaGraphDestroy(L.graph);
+  L.gexec = nullptr;
+  L.graph = nullptr;
+  L.graph_key.clear();
+}
+void drop_graph(mppi_batch* b) { drop_lane_graph(b->lane); }
+
+void free_lane(BatchLane& L) {
+  if (L.last) cudaStreamSynchronize(L.last);
+  drop_lane_graph(L);
+  cudaFreeHost(L.h_stage);
+  cudaFree(L.d_stage);
+  cudaFreeHost(L.h_out);
+  cudaFree(L.d_out);
+  L = BatchLane();
 }
 
 // Device bytes of one slot (laid out in this order by slot_layout).
@@ -1065,7 +1089,6 @@ int mppi_batch_create(int32_t max_ctrl, size_t pool_bytes, mppi_batch** out) {
   }
   b->pool_bytes = pool_bytes;
   b->free_list.push_back({0, pool_bytes});
-  b->last = b->own;
   batch_max_smem(b);
   *out = b;
   return MPPI_OK;
@@ -1167,7 +1190,7 @@ int mppi_batch_set_obstacles(mppi_batch* b, int32_t slot, const double* cxcyr, i
   int rc = choose_tiling(&s.p, &s.tl, J, &t, &smem);
   if (rc) return rc;
   if (smem > batch_max_smem(b)) return fail(MPPI_EINVAL, "obstacle set too large");
-  CK(cudaStreamSynchronize(b->last));
+  if (b->lane.last) CK(cudaStreamSynchronize(b->lane.last));
   if (J > s.Jcap) {
     // grow the slot: a new range holding the state and the larger obstacle area
     const size_t nbytes = slot_bytes(&s.p, &s.tl, J);
@@ -1197,7 +1220,7 @@ int mppi_batch_remove(mppi_batch* b, int32_t slot) {
   if (!b) return fail(MPPI_ESTATE, "batch is NULL");
   if (slot < 0 || slot >= b->max_ctrl || !b->slots[slot].used)
     return fail(MPPI_EINVAL, "slot %d is not in use", slot);
-  CK(cudaStreamSynchronize(b->last));
+  if (b->lane.last) CK(cudaStreamSynchronize(b->lane.last));
   BatchSlot& s = b->slots[slot];
   pool_free(b, s.off, s.bytes);
   s.used = false;
@@ -1205,13 +1228,15 @@ int mppi_batch_remove(mppi_batch* b, int32_t slot) {
   return MPPI_OK;
 }
 
-int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double* x0s,
-                    const double* const* xrefs, void* stream) {
-  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
-  if (n < 0 || (n > 0 && (!slots || !x0s))) return fail(MPPI_EINVAL, "bad slot list");
-  cudaStream_t st = stream ? (cudaStream_t)stream : b->own;
-  if (n == 0) return MPPI_OK;
-  // validate, compute sizes
+}  // extern "C"
+
+namespace {
+
+// One batched step of the listed slots on lane L and stream st: pack, copy
+// in, launch, copy out; graph replay when allowed and the composition is the
+// one captured.  Slot bookkeeping must not change concurrently.
+int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, const double* x0s,
+              const double* const* xrefs, cudaStream_t st, bool allow_graph) {
   size_t n_items = 0, n_in = 0;
   int smem = 0;
   std::vector<int> order(n);
@@ -1230,41 +1255,40 @@ int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double
   const size_t head = sizeof(BatchHdr) + sizeof(StepEntry) * n + sizeof(WorkItem) * n_items;
   const size_t inputs_off = (head + 15) & ~(size_t)15;
   const size_t bytes = inputs_off + sizeof(double) * n_in;
-  // staging buffers
-  if (b->last) CK(cudaStreamSynchronize(b->last));
-  if (bytes > b->stage_cap) {
-    drop_graph(b);
-    cudaFreeHost(b->h_stage);
-    cudaFree(b->d_stage);
-    b->h_stage = nullptr;
-    b->d_stage = nullptr;
+  if (L.last) CK(cudaStreamSynchronize(L.last));
+  if (bytes > L.stage_cap) {
+    drop_lane_graph(L);
+    cudaFreeHost(L.h_stage);
+    cudaFree(L.d_stage);
+    L.h_stage = nullptr;
+    L.d_stage = nullptr;
     size_t cap = std::max(bytes, (size_t)1 << 16) * 2;
-    if (cudaMallocHost((void**)&b->h_stage, cap) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_stage, cap) != cudaSuccess) {
+    if (cudaMallocHost((void**)&L.h_stage, cap) != cudaSuccess ||
+        cudaMalloc((void**)&L.d_stage, cap) != cudaSuccess) {
       cudaGetLastError();
-      b->stage_cap = 0;
+      L.stage_cap = 0;
       return fail(MPPI_ENOMEM, "staging allocation failed");
     }
-    b->stage_cap = cap;
+    L.stage_cap = cap;
   }
-  if (n > b->u0_cap) {
-    drop_graph(b);
-    cudaFreeHost(b->h_u0);
-    cudaFree(b->d_u0);
+  if (n > L.out_cap) {
+    drop_lane_graph(L);
+    cudaFreeHost(L.h_out);
+    cudaFree(L.d_out);
     int cap = std::max(n, 64) * 2;
-    if (cudaMallocHost((void**)&b->h_u0, sizeof(double) * 2 * cap) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_u0, sizeof(double) * 2 * cap) != cudaSuccess) {
+    if (cudaMallocHost((void**)&L.h_out, sizeof(double) * 8 * cap) != cudaSuccess ||
+        cudaMalloc((void**)&L.d_out, sizeof(double) * 8 * cap) != cudaSuccess) {
       cudaGetLastError();
-      b->u0_cap = 0;
+      L.out_cap = 0;
       return fail(MPPI_ENOMEM, "output allocation failed");
     }
-    b->u0_cap = cap;
+    L.out_cap = cap;
   }
   // pack: header, step table, longest-first work items, inputs
-  BatchHdr* hdr = (BatchHdr*)b->h_stage;
-  StepEntry* steps = (StepEntry*)(b->h_stage + sizeof(BatchHdr));
+  BatchHdr* hdr = (BatchHdr*)L.h_stage;
+  StepEntry* steps = (StepEntry*)(L.h_stage + sizeof(BatchHdr));
   WorkItem* items = (WorkItem*)(steps + n);
-  double* in = (double*)(b->h_stage + inputs_off);
+  double* in = (double*)(L.h_stage + inputs_off);
   std::sort(order.begin(), order.end(), [&](int a, int c) {
     return b->slots[slots[a]].tile_cost > b->slots[slots[c]].tile_cost;
   });
@@ -1280,7 +1304,8 @@ int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double
     d += nn;
     steps[i].xref_off = (int)d;
     const double* xr = xrefs ? xrefs[i] : nullptr;
-    if (xr && !finite_all(xr, (T + 1) * nn)) return fail(MPPI_EINVAL, "xref of slot %d is not finite", slots[i]);
+    if (xr && !finite_all(xr, (T + 1) * nn))
+      return fail(MPPI_EINVAL, "xref of slot %d is not finite", slots[i]);
     for (int t = 0; t <= T; ++t)
       for (int k = 0; k < nn; ++k) in[d + t * nn + k] = xr ? xr[t * nn + k] : s.p.x_goal[k];
     d += (size_t)(T + 1) * nn;
@@ -1299,39 +1324,55 @@ int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double
   if (occ < 1) return fail(MPPI_EINVAL, "batch needs %d bytes of shared memory per CTA", smem);
   const int grid = (int)std::min<size_t>((size_t)num_sms() * occ, n_items);
   std::vector<int> key(slots, slots + n);
-  const bool same = b->use_graph && b->gexec && key == b->graph_key && bytes == b->graph_bytes &&
-                    smem == b->graph_smem && grid == b->graph_grid && st == b->last;
+  const bool same = allow_graph && L.gexec && key == L.graph_key && bytes == L.graph_bytes &&
+                    smem == L.graph_smem && grid == L.graph_grid && st == L.last;
   if (same) {
-    CK(cudaGraphLaunch(b->gexec, st));
+    CK(cudaGraphLaunch(L.gexec, st));
   } else {
-    drop_graph(b);
-    bool capture = b->use_graph != 0;
-    if (capture) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaMemcpyAsync(b->d_stage, b->h_stage, bytes, cudaMemcpyHostToDevice, st);
-    batch_kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, b->d_stage, b->d_u0);
-    cudaMemcpyAsync(b->h_u0, b->d_u0, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st);
-    if (capture) {
-      CK(cudaStreamEndCapture(st, &b->graph));
-      CK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
-      b->graph_key = key;
-      b->graph_bytes = bytes;
-      b->graph_smem = smem;
-      b->graph_grid = grid;
-      CK(cudaGraphLaunch(b->gexec, st));
+    drop_lane_graph(L);
+    if (allow_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(L.d_stage, L.h_stage, bytes, cudaMemcpyHostToDevice, st);
+    batch_kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, L.d_stage, L.d_out);
+    cudaMemcpyAsync(L.h_out, L.d_out, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st);
+    if (allow_graph) {
+      CK(cudaStreamEndCapture(st, &L.graph));
+      CK(cudaGraphInstantiate(&L.gexec, L.graph, 0));
+      L.graph_key = key;
+      L.graph_bytes = bytes;
+      L.graph_smem = smem;
+      L.graph_grid = grid;
+      CK(cudaGraphLaunch(L.gexec, st));
     } else {
       CK(cudaGetLastError());
     }
   }
-  b->last = st;
-  b->n_last = n;
+  L.last = st;
+  L.n_last = n;
   return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mppi_batch_step(mppi_batch* b, const int32_t* slots, int32_t n, const double* x0s,
+                    const double* const* xrefs, void* stream) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (n < 0 || (n > 0 && (!slots || !x0s))) return fail(MPPI_EINVAL, "bad slot list");
+  cudaStream_t st = stream ? (cudaStream_t)stream : b->own;
+  if (n == 0) return MPPI_OK;
+  return lane_step(b, b->lane, slots, n, x0s, xrefs, st, b->use_graph != 0);
 }
 
 int mppi_batch_get_controls(mppi_batch* b, double* u0s, int32_t n) {
   if (!b) return fail(MPPI_ESTATE, "batch is NULL");
-  if (n != b->n_last) return fail(MPPI_EINVAL, "n=%d but the last step had %d controllers", n, b->n_last);
-  CK(cudaStreamSynchronize(b->last));
-  if (u0s && n > 0) memcpy(u0s, b->h_u0, sizeof(double) * 2 * n);
+  BatchLane& L = b->lane;
+  if (n != L.n_last) return fail(MPPI_EINVAL, "n=%d but the last step had %d controllers", n, L.n_last);
+  if (L.last) CK(cudaStreamSynchronize(L.last));
+  for (int i = 0; u0s && i < n; ++i) {
+    u0s[2 * i] = L.h_out[8 * i];
+    u0s[2 * i + 1] = L.h_out[8 * i + 1];
+  }
   return MPPI_OK;
 }
 
@@ -1339,7 +1380,7 @@ int mppi_batch_get_state(mppi_batch* b, int32_t slot, double* U, double* costs, 
   if (!b) return fail(MPPI_ESTATE, "batch is NULL");
   if (slot < 0 || slot >= b->max_ctrl || !b->slots[slot].used)
     return fail(MPPI_EINVAL, "slot %d is not in use", slot);
-  CK(cudaStreamSynchronize(b->last));
+  if (b->lane.last) CK(cudaStreamSynchronize(b->lane.last));
   const BatchSlot& s = b->slots[slot];
   if (U) CK(cudaMemcpy(U, s.D.U, sizeof(double) * 2 * s.p.T, cudaMemcpyDeviceToHost));
   if (costs) CK(cudaMemcpy(costs, s.D.costs, sizeof(double) * s.p.K, cudaMemcpyDeviceToHost));
@@ -1379,7 +1420,7 @@ int mppi_batch_info(mppi_batch* b, int32_t slot, mppi_tiling* t, uint64_t* bytes
 
 int mppi_batch_set_graph(mppi_batch* b, int32_t enable) {
   if (!b) return fail(MPPI_ESTATE, "batch is NULL");
-  if (b->last) CK(cudaStreamSynchronize(b->last));
+  if (b->lane.last) CK(cudaStreamSynchronize(b->lane.last));
   drop_graph(b);
   b->use_graph = enable ? 1 : 0;
   return MPPI_OK;
@@ -1387,16 +1428,276 @@ int mppi_batch_set_graph(mppi_batch* b, int32_t enable) {
 
 int mppi_batch_destroy(mppi_batch* b) {
   if (!b) return MPPI_OK;
-  if (b->last) cudaStreamSynchronize(b->last);
-  drop_graph(b);
+  free_lane(b->lane);
   cudaFree(b->pool);
   cudaFree(b->d_descs);
-  cudaFreeHost(b->h_stage);
-  cudaFree(b->d_stage);
-  cudaFreeHost(b->h_u0);
-  cudaFree(b->d_u0);
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
+  return MPPI_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Serving runtime: continuous batching of control-step requests from many
+// robots.  Robots join by taking a slot of the device pool (admission by
+// memory); their warm-start sequence, generator counter, exploration rate
+// and barrier state stay on the device between requests.  A scheduler thread
+// keeps up to `lanes` batched steps in flight, each on its own stream: when a
+// lane is free it launches one persistent batch holding every request queued
+// so far, so requests that arrive while others run join the next batch and
+// the batches overlap on the device.  Completions carry u*_0, the model's
+// prediction of the next state and the latency from submission.
+
+namespace {
+
+struct ServerReq {
+  int robot;
+  double x0[6];
+  std::vector<double> xref;  // empty: goal repeated
+  std::chrono::steady_clock::time_point t0;
+};
+
+struct ServerDone {
+  int robot;
+  double out[8];  // u0[2], x1[6]
+  double latency;
+  int status;
+};
+
+}  // namespace
+
+struct mppi_server {
+  mppi_batch* b = nullptr;
+  int max_robots = 0;
+  std::vector<BatchLane> lanes;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  std::vector<std::vector<ServerReq>> inflight;
+  std::vector<char> lane_busy;
+  std::mutex mu;  // queue, completions, robot flags and the slot bookkeeping
+  std::deque<ServerReq> queue;
+  std::deque<ServerDone> done;
+  std::vector<char> joined, busy;
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  std::atomic<unsigned long long> batches{0}, requests{0};
+  std::atomic<int> n_inflight{0};
+  char err[256] = "";
+};
+
+namespace {
+
+void server_loop(mppi_server* sv) {
+  std::vector<int32_t> slots;
+  std::vector<double> x0s;
+  std::vector<const double*> xr;
+  while (!sv->stop.load()) {
+    bool did = false;
+    for (size_t i = 0; i < sv->lanes.size(); ++i) {
+      if (!sv->lane_busy[i]) continue;
+      cudaError_t q = cudaEventQuery(sv->events[i]);
+      if (q == cudaErrorNotReady) continue;
+      const auto now = std::chrono::steady_clock::now();
+      std::lock_guard<std::mutex> g(sv->mu);
+      const double* out = sv->lanes[i].h_out;
+      for (size_t j = 0; j < sv->inflight[i].size(); ++j) {
+        const ServerReq& r = sv->inflight[i][j];
+        ServerDone d;
+        d.robot = r.robot;
+        for (int k = 0; k < 8; ++k) d.out[k] = q == cudaSuccess ? out[8 * j + k] : NAN;
+        d.latency = std::chrono::duration<double>(now - r.t0).count();
+        d.status = q == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
+        sv->done.push_back(d);
+        sv->busy[r.robot] = 0;
+      }
+      sv->n_inflight -= (int)sv->inflight[i].size();
+      sv->requests += sv->inflight[i].size();
+      sv->inflight[i].clear();
+      sv->lane_busy[i] = 0;
+      did = true;
+    }
+    for (size_t i = 0; i < sv->lanes.size(); ++i) {
+      if (sv->lane_busy[i]) continue;
+      std::lock_guard<std::mutex> g(sv->mu);
+      if (sv->queue.empty()) break;
+      std::vector<ServerReq>& batch = sv->inflight[i];
+      batch.clear();
+      while (!sv->queue.empty()) {
+        batch.push_back(std::move(sv->queue.front()));
+        sv->queue.pop_front();
+      }
+      const int n = (int)batch.size();
+      slots.resize(n);
+      x0s.assign((size_t)n * 6, 0.0);
+      xr.resize(n);
+      for (int j = 0; j < n; ++j) {
+        slots[j] = batch[j].robot;
+        memcpy(&x0s[(size_t)j * 6], batch[j].x0, sizeof(double) * 6);
+        xr[j] = batch[j].xref.empty() ? nullptr : batch[j].xref.data();
+      }
+      int rc = lane_step(sv->b, sv->lanes[i], slots.data(), n, x0s.data(), xr.data(),
+                         sv->streams[i], false);
+      if (rc == MPPI_OK) rc = cudaEventRecord(sv->events[i], sv->streams[i]) == cudaSuccess
+                                  ? MPPI_OK : MPPI_ECUDA;
+      if (rc != MPPI_OK) {
+        snprintf(sv->err, sizeof(sv->err), "%s", g_err);
+        const auto now = std::chrono::steady_clock::now();
+        for (const ServerReq& r : batch) {
+          ServerDone d;
+          d.robot = r.robot;
+          for (int k = 0; k < 8; ++k) d.out[k] = NAN;
+          d.latency = std::chrono::duration<double>(now - r.t0).count();
+          d.status = rc;
+          sv->done.push_back(d);
+          sv->busy[r.robot] = 0;
+        }
+        sv->n_inflight -= n;
+        batch.clear();
+        continue;
+      }
+      sv->lane_busy[i] = 1;
+      sv->batches++;
+      did = true;
+    }
+    if (!did) std::this_thread::sleep_for(std::chrono::microseconds(10));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes, mppi_server** out) {
+  if (!out) return fail(MPPI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (lanes < 1 || lanes > 8) return fail(MPPI_EINVAL, "lanes must be in [1, 8]");
+  mppi_server* sv = new (std::nothrow) mppi_server();
+  if (!sv) return fail(MPPI_ENOMEM, "host allocation failed");
+  int rc = mppi_batch_create(max_robots, pool_bytes, &sv->b);
+  if (rc) {
+    delete sv;
+    return rc;
+  }
+  sv->max_robots = max_robots;
+  sv->lanes.resize(lanes);
+  sv->streams.resize(lanes);
+  sv->events.resize(lanes);
+  sv->inflight.resize(lanes);
+  sv->lane_busy.assign(lanes, 0);
+  sv->joined.assign(max_robots, 0);
+  sv->busy.assign(max_robots, 0);
+  for (int i = 0; i < lanes; ++i) {
+    if (cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->events[i], cudaEventDisableTiming) != cudaSuccess) {
+      mppi_batch_destroy(sv->b);
+      delete sv;
+      return fail(MPPI_ECUDA, "stream/event creation failed");
+    }
+  }
+  sv->worker = std::thread(server_loop, sv);
+  *out = sv;
+  return MPPI_OK;
+}
+
+int mppi_server_join(mppi_server* sv, const mppi_params* p, const double* u_init,
+                     const double* cxcyr, int32_t J, int32_t* robot) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  std::lock_guard<std::mutex> g(sv->mu);
+  int32_t slot = -1;
+  int rc = mppi_batch_add(sv->b, p, u_init, nullptr, cxcyr, J, &slot);
+  if (rc) return rc;
+  sv->joined[slot] = 1;
+  sv->busy[slot] = 0;
+  *robot = slot;
+  return MPPI_OK;
+}
+
+int mppi_server_leave(mppi_server* sv, int32_t robot) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (robot < 0 || robot >= sv->max_robots || !sv->joined[robot])
+    return fail(MPPI_EINVAL, "robot %d has not joined", robot);
+  if (sv->busy[robot]) return fail(MPPI_ESTATE, "robot %d has a request in flight", robot);
+  int rc = mppi_batch_remove(sv->b, robot);
+  if (rc) return rc;
+  sv->joined[robot] = 0;
+  return MPPI_OK;
+}
+
+int mppi_server_submit(mppi_server* sv, int32_t robot, const double* x0, const double* xref) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  if (!x0) return fail(MPPI_EINVAL, "x0 is NULL");
+  ServerReq r;
+  r.robot = robot;
+  r.t0 = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (robot < 0 || robot >= sv->max_robots || !sv->joined[robot])
+    return fail(MPPI_EINVAL, "robot %d has not joined", robot);
+  if (sv->busy[robot]) return fail(MPPI_ESTATE, "robot %d already has a request", robot);
+  const BatchSlot& s = sv->b->slots[robot];
+  for (int k = 0; k < 6; ++k) r.x0[k] = k < s.n ? x0[k] : 0.0;
+  if (!finite_all(r.x0, s.n)) return fail(MPPI_EINVAL, "x0 is not finite");
+  if (xref) {
+    r.xref.assign(xref, xref + (size_t)(s.p.T + 1) * s.n);
+    if (!finite_all(r.xref.data(), (int)r.xref.size())) return fail(MPPI_EINVAL, "xref is not finite");
+  }
+  sv->busy[robot] = 1;
+  sv->n_inflight++;
+  sv->queue.push_back(std::move(r));
+  return MPPI_OK;
+}
+
+int mppi_server_poll(mppi_server* sv, int32_t max, int32_t* robots, double* u0s, double* x1s,
+                     double* latency_s, int32_t* status, int32_t* n_out) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  if (!n_out) return fail(MPPI_EINVAL, "n_out is NULL");
+  std::lock_guard<std::mutex> g(sv->mu);
+  int n = 0;
+  while (n < max && !sv->done.empty()) {
+    const ServerDone& d = sv->done.front();
+    if (robots) robots[n] = d.robot;
+    if (u0s) {
+      u0s[2 * n] = d.out[0];
+      u0s[2 * n + 1] = d.out[1];
+    }
+    if (x1s)
+      for (int k = 0; k < 6; ++k) x1s[6 * n + k] = d.out[2 + k];
+    if (latency_s) latency_s[n] = d.latency;
+    if (status) status[n] = d.status;
+    sv->done.pop_front();
+    ++n;
+  }
+  *n_out = n;
+  return MPPI_OK;
+}
+
+int mppi_server_stats(mppi_server* sv, uint64_t* batches, uint64_t* requests, int32_t* pending,
+                      uint64_t* pool_free_bytes) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  if (batches) *batches = sv->batches.load();
+  if (requests) *requests = sv->requests.load();
+  if (pending) *pending = sv->n_inflight.load();
+  if (pool_free_bytes) {
+    std::lock_guard<std::mutex> g(sv->mu);
+    size_t f = 0;
+    for (auto& e : sv->b->free_list) f += e.second;
+    *pool_free_bytes = f;
+  }
+  return MPPI_OK;
+}
+
+int mppi_server_destroy(mppi_server* sv) {
+  if (!sv) return MPPI_OK;
+  sv->stop = true;
+  if (sv->worker.joinable()) sv->worker.join();
+  for (size_t i = 0; i < sv->lanes.size(); ++i) {
+    free_lane(sv->lanes[i]);
+    cudaEventDestroy(sv->events[i]);
+    cudaStreamDestroy(sv->streams[i]);
+  }
+  mppi_batch_destroy(sv->b);
+  delete sv;
   return MPPI_OK;
 }
 

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const CtrlDesc* __
     __syncthreads();
     const double* x0 = inputs + e.x0_off;
     const double* xref = inputs + e.xref_off;
-    double* uo = u0_out + 2 * w.ctrl;
+    double* uo = u0_out + 8 * w.ctrl;  // u0 and the predicted next state
     switch (Ds.model * 2 + npos_code(Ds.NPOS)) {
       case 0: run_tile<0, 8>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
       case 1: run_tile<0, 14>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;

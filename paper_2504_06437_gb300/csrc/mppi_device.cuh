@@ -55,6 +55,7 @@ struct DevState {
   double beta_d;     // last step: barrier summed at the goal pose
   double S_e_used;   // last step: exploration rate of the draws
   double u0[2];      // last step: u*_0
+  double x1[6];      // last step: state after applying u*_0 (model prediction)
   double C0;         // sum_t gamma u_t^T (S_e Sigma)^-1 u_t of the next step
   double csum, g1;   // DBaS unrolling constants (see above)
   float L00, L10, L11, pad;  // chol(S_e Sigma) of the next step

@@ -95,7 +95,8 @@ template <int MODEL, bool COST>
 __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int vs,
                                 const float* __restrict__ x_init, float4* pose, int ps,
                                 const float2* __restrict__ Uf, const float2* __restrict__ Af,
-                                const float* __restrict__ xrf, FF& cost, int lane) {
+                                const float* __restrict__ xrf, FF& cost, int lane,
+                                float* x1 = nullptr) {
   const float dt = D.dt;
   if constexpr (MODEL == 0) {
     float cth = x_init[2], cx = x_init[0], cy = x_init[1];
@@ -112,6 +113,11 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
       const float vdt = v.x * dt;
       const float xa = cx + warp_incl_scan(vdt * cb, lane);
       const float ya = cy + warp_incl_scan(vdt * sb, lane);
+      if (x1 && t == 0) {
+        x1[0] = xa;
+        x1[1] = ya;
+        x1[2] = th_a;
+      }
       if (valid) {
         pose[t * ps] = make_float4(xa, ya, ca, sa);
         if constexpr (COST) {
@@ -155,6 +161,14 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
       const float vy_b = from_prev_lane(vy_a, cvy, lane), vz_b = from_prev_lane(vz_a, cvz, lane);
       const float y_a = cy + warp_incl_scan(vy_b * dt, lane);
       const float z_a = cz + warp_incl_scan(vz_b * dt, lane);
+      if (x1 && t == 0) {
+        x1[0] = y_a;
+        x1[1] = z_a;
+        x1[2] = ph_a;
+        x1[3] = vy_a;
+        x1[4] = vz_a;
+        x1[5] = w_a;
+      }
       if (valid) {
         pose[t * ps] = make_float4(y_a, z_a, ca, sa);
         if constexpr (COST) {
@@ -198,7 +212,7 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // S_e (Eq. 10, C_B floored at 0 inside the logarithm), shift, state update.
 template <int MODEL, int NPOS>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
-                            double* u0_out) {
+                            const double* __restrict__ x0g, double* out) {
   const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31;
   const int T = D.T, P = D.P;
   double* Us = reinterpret_cast<double*>(smem + L.Us);
@@ -223,10 +237,11 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
     D.Ustar[c] = u;
   }
   __syncthreads();
+  float* x1 = reinterpret_cast<float*>(smem + L.scH);  // per-sample sums are consumed
   if (tid < 32) {
     FF none = {0.0f, 0.0f};
     scan_trajectory<MODEL, false>(D, T, Usf, 1, xi, pose_nom, 1, nullptr, nullptr, nullptr, none,
-                                  lane);
+                                  lane, x1);
   }
   __syncthreads();
   barrier_flat(T * P, P, D.J, pose_nom, shp, obs4, D.h_eps, b_nom, tid, nthreads);
@@ -254,9 +269,16 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       st->S_e_used = S_e_used;
       st->u0[0] = Us[0];
       st->u0[1] = Us[1];
-      if (u0_out) {
-        u0_out[0] = Us[0];
-        u0_out[1] = Us[1];
+      constexpr int n = Dyn<MODEL>::n;
+      double xn[6] = {0, 0, 0, 0, 0, 0};
+      xn[0] = x0g[0] + (double)x1[0];  // back from the frame centred on x0
+      xn[1] = x0g[1] + (double)x1[1];
+      for (int d = 2; d < n; ++d) xn[d] = (double)x1[d];
+      for (int d = 0; d < 6; ++d) st->x1[d] = xn[d];
+      if (out) {  // batched launches: u0 then the predicted state, 8 doubles
+        out[0] = Us[0];
+        out[1] = Us[1];
+        for (int d = 0; d < 6; ++d) out[2 + d] = xn[d];
       }
       st->S_e = S_e_next;
       st->beta = ts.beta0;
@@ -516,7 +538,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z, col_hi,
                  col_lo, mbuf, tid, nthreads);
   if (tid == 0) D.counters[D.nGroups] = 0u;
-  final_stage<MODEL, NPOS>(D, smem, L, ts, u0_out);
+  final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
 }
 
 }  // namespace dbm

@@ -1,0 +1,120 @@
+"""Continuous-batching serving runtime on the GPU: requests that arrive
+while batches are in flight are served by later, overlapping batches; each
+robot's result is the same, bit for bit, as the robot alone through the
+context API with the same launch shape; admission by memory."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2504_06437_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06437_gb300 import binding
+    binding.build()
+    binding.load()
+    return binding
+
+
+def wait_all(srv, n, timeout=60.0):
+    got = []
+    t0 = time.time()
+    while len(got) < n:
+        got += srv.poll()
+        assert time.time() - t0 < timeout, "requests did not complete"
+    return got
+
+
+def test_served_results_equal_alone(gpu):
+    g = W.rng(11)
+    worlds = [W._mixed_world(g, i, 11, 256, 6000, 10, 60, 5, 120) for i in range(7)]
+    rounds = 3
+    with gpu.Server(16, 512 << 20, lanes=2) as srv:
+        robots = [srv.join(w.params, w.obstacles) for w in worlds]
+        assert all(r is not None for r in robots)
+        x = {r: w.x_start.copy() for r, w in zip(robots, worlds)}
+        xs = {r: [] for r in robots}
+        us = {r: [] for r in robots}
+        pending = set()
+        # staggered arrivals: robots submit at different times, while
+        # earlier batches are still on the GPU
+        order = list(robots)
+        done_rounds = {r: 0 for r in robots}
+        for r in order:
+            xs[r].append(x[r].copy())
+            srv.submit(r, x[r], worlds[robots.index(r)].reference(x[r]))
+            pending.add(r)
+            time.sleep(0.0005)
+        t0 = time.time()
+        while pending:
+            for (r, u0, x1, lat, st) in srv.poll():
+                assert st == 0 and lat > 0
+                us[r].append(u0.copy())
+                pending.discard(r)
+                done_rounds[r] += 1
+                if done_rounds[r] < rounds:
+                    w = worlds[robots.index(r)]
+                    x[r] = x1[: w.n].copy()
+                    xs[r].append(x[r].copy())
+                    srv.submit(r, x[r], w.reference(x[r]))
+                    pending.add(r)
+            assert time.time() - t0 < 60
+        st = srv.stats()
+        assert st["requests"] == rounds * len(robots)
+        assert st["batches"] < st["requests"]          # requests were batched
+    for r, w in zip(robots, worlds):
+        p = w.params
+        S = min(32, p["K"])
+        # the slot's launch shape: samples_per_cta as admitted (32, halved to fit)
+        with gpu.Batch(2, 64 << 20) as b:
+            sl = b.add(p, w.obstacles)
+            info = b.slot_info(sl)
+        with gpu.Controller(p, tiling=dict(samples_per_cta=info["samples_per_cta"], threads=256,
+                                           positions_per_thread=info["positions_per_thread"])) as c:
+            c.set_obstacles(w.obstacles)
+            for k in range(rounds):
+                c.step(xs[r][k], w.reference(xs[r][k]))
+                np.testing.assert_array_equal(c.get_control(), us[r][k])
+
+
+def test_admission_refused_then_granted(gpu):
+    w = W.quad2d(2, K=8192, T=60)
+    with gpu.Server(64, 4 << 20, lanes=1) as srv:
+        robots = []
+        while True:
+            r = srv.join(w.params, w.obstacles)
+            if r is None:
+                break
+            robots.append(r)
+            assert len(robots) < 64
+        assert robots
+        srv.submit(robots[0], w.x_start)
+        wait_all(srv, 1)
+        srv.leave(robots[0])
+        r = srv.join(w.params, w.obstacles)
+        assert r is not None
+        srv.submit(r, w.x_start)
+        (rid, u0, x1, lat, st), = wait_all(srv, 1)
+        assert rid == r and st == 0 and np.all(np.isfinite(u0))
+
+
+def test_many_requests_complete(gpu):
+    g = W.rng(5)
+    worlds = [W._mixed_world(g, i, 5, 128, 2048, 10, 40, 5, 60) for i in range(40)]
+    with gpu.Server(64, 512 << 20, lanes=3) as srv:
+        robots = [srv.join(w.params, w.obstacles) for w in worlds]
+        for r, w in zip(robots, worlds):
+            srv.submit(r, w.x_start)
+        got = wait_all(srv, len(robots))
+        assert sorted(x[0] for x in got) == sorted(robots)
+        with pytest.raises(gpu.MppiError):
+            srv.submit(robots[0], worlds[0].x_start)
+            srv.submit(robots[0], worlds[0].x_start)    # second while the first is queued
+        wait_all(srv, 1)
