@@ -456,6 +456,8 @@ def main():
     ap.add_argument("--load", type=float, default=0.5)
     ap.add_argument("--plain-robots", type=int, default=100)
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--tiling", default="",
+                    help="explicit launch shape S,threads,points (skips the autotuner)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default launch shape instead of the autotuned one")
     args = ap.parse_args()
@@ -483,7 +485,10 @@ def main():
     P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
     J = int(world.obstacles.shape[0])
     tiling, tune_us = None, None
-    if not args.no_autotune:
+    if args.tiling:
+        S_, NT_, NP_ = (int(v) for v in args.tiling.split(","))
+        tiling = dict(samples_per_cta=S_, threads=NT_, positions_per_thread=NP_)
+    elif not args.no_autotune:
         tiling, tune_us = binding.autotune(p, world.obstacles, iters=10)
     ctl = binding.Controller(p, tiling=tiling)
     ctl.set_obstacles(world.obstacles)
@@ -559,7 +564,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(describe(world), parallelism=f"replicas x{ws}", tiling=tiling,
-                           tiling_source="autotuned" if tune_us else "default"),
+                           tiling_source="autotuned" if tune_us else ("explicit" if args.tiling else "default")),
             "latency_ms": {"p50": float(np.percentile(times_ms, 50)),
                            "p99": float(np.percentile(times_ms, 99))},
             "e2e": {"value": ws * K * T / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -131,6 +131,14 @@ int validate(const mppi_params* p) {
   return MPPI_OK;
 }
 
+// Tiles merged by one CTA: all of them in one level up to 256 tiles, else
+// groups of at least 32 so that at most 64 group results remain.
+int group_size(int nTiles) {
+  if (nTiles <= 256) return nTiles;
+  int GT = (nTiles + 63) / 64;
+  return GT < 32 ? 32 : GT;
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -251,8 +259,7 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
   const int limit = max_smem_optin();
   for (;;) {
     const int nTiles = (p->K + t.samples_per_cta - 1) / t.samples_per_cta;
-    int GT = (nTiles + 63) / 64;
-    if (GT < 32) GT = 32;
+    const int GT = group_size(nTiles);
     const int nGroups = (nTiles + GT - 1) / GT;
     const int nscl = GT > nGroups ? GT : nGroups;
     SmemLayout L = smem_layout(p->T, t.samples_per_cta, p->n_shape, J, n, nscl, t.threads / 32);
@@ -285,8 +292,7 @@ void fill_desc(mppi_ctx* c) {
   D.S = c->tl.samples_per_cta;
   D.NPOS = c->tl.positions_per_thread;
   D.nTiles = (p->K + D.S - 1) / D.S;
-  D.GT = (D.nTiles + 63) / 64;
-  if (D.GT < 32) D.GT = 32;
+  D.GT = group_size(D.nTiles);
   D.nGroups = (D.nTiles + D.GT - 1) / D.GT;
   D.nscl = D.GT > D.nGroups ? D.GT : D.nGroups;
   D.dt = (float)p->dt;
@@ -387,8 +393,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   }
   const int T = p->T, K = p->K, n = c->n;
   const int nTiles = (K + c->tl.samples_per_cta - 1) / c->tl.samples_per_cta;
-  int GT = (nTiles + 63) / 64;
-  if (GT < 32) GT = 32;
+  const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
 #define ALLOC(ptr, bytes)                                                          \
   do {                                                                             \
@@ -750,8 +755,7 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   if (rc) return rc;
   const int T = p->T, K = p->K;
   const int nTiles = (K + c.tl.samples_per_cta - 1) / c.tl.samples_per_cta;
-  int GT = (nTiles + 63) / 64;
-  if (GT < 32) GT = 32;
+  const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
   size_t off = 0;
   const size_t o_st = carve(&off, sizeof(DevState));
@@ -987,8 +991,7 @@ void free_lane(BatchLane& L) {
 size_t slot_bytes(const mppi_params* p, const mppi_tiling* t, int Jcap) {
   const int T = p->T, K = p->K;
   const int nTiles = (K + t->samples_per_cta - 1) / t->samples_per_cta;
-  int GT = (nTiles + 63) / 64;
-  if (GT < 32) GT = 32;
+  const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
   size_t off = 0;
   carve(&off, sizeof(double) * 2 * T);
@@ -1012,8 +1015,7 @@ void slot_layout(mppi_batch* b, BatchSlot& s, mppi_ctx* c) {
   const mppi_params* p = &s.p;
   const int T = p->T, K = p->K;
   const int nTiles = (K + s.tl.samples_per_cta - 1) / s.tl.samples_per_cta;
-  int GT = (nTiles + 63) / 64;
-  if (GT < 32) GT = 32;
+  const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
   unsigned char* base = b->pool + s.off;
   size_t off = 0;
@@ -1483,7 +1485,7 @@ struct mppi_server {
   std::atomic<bool> stop{false};
   std::atomic<unsigned long long> batches{0}, requests{0};
   std::atomic<int> n_inflight{0};
-  char err[256] = "";
+  char err[512] = "";
 };
 
 namespace {

@@ -447,28 +447,35 @@ __device__ inline void merge_partials_nj(int n, const float4* rz, const float* c
   };
   load_batch(i0);  // issued before the minima are known
   if (warp == 0) {
+    // all (rho_i, Z_i) of this lane's sources in flight at once
+    constexpr int RZ = 4;
     const float inf = __int_as_float(0x7f800000);
-    const float4 a = lane < n ? __ldcg(&rz[lane]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
-    const float4 b = lane + 32 < n ? __ldcg(&rz[lane + 32]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
-    FF r = FF{a.x, a.y};
-    if (ff_less(FF{b.x, b.y}, r)) r = FF{b.x, b.y};
-    for (int i = lane + 64; i < n; i += 32) {
+    float4 rr[RZ];
+#pragma unroll
+    for (int q = 0; q < RZ; ++q) {
+      const int i = lane + 32 * q;
+      rr[q] = i < n ? __ldcg(&rz[i]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
+    }
+    FF r = FF{rr[0].x, rr[0].y};
+#pragma unroll
+    for (int q = 1; q < RZ; ++q)
+      if (ff_less(FF{rr[q].x, rr[q].y}, r)) r = FF{rr[q].x, rr[q].y};
+    for (int i = lane + 32 * RZ; i < n; i += 32) {
       const float4 c = __ldcg(&rz[i]);
       if (ff_less(FF{c.x, c.y}, r)) r = FF{c.x, c.y};
     }
     r = warp_min_ff(r);
     FF z = {0.0f, 0.0f};
-    if (lane < n) {
-      const float sc = expf(-ff_diff(FF{a.x, a.y}, r) * inv_lambda);
-      scl[lane] = sc;
-      ff_add_prod(z, sc, a.z, a.w);
+#pragma unroll
+    for (int q = 0; q < RZ; ++q) {
+      const int i = lane + 32 * q;
+      if (i < n) {
+        const float sc = expf(-ff_diff(FF{rr[q].x, rr[q].y}, r) * inv_lambda);
+        scl[i] = sc;
+        ff_add_prod(z, sc, rr[q].z, rr[q].w);
+      }
     }
-    if (lane + 32 < n) {
-      const float sc = expf(-ff_diff(FF{b.x, b.y}, r) * inv_lambda);
-      scl[lane + 32] = sc;
-      ff_add_prod(z, sc, b.z, b.w);
-    }
-    for (int i = lane + 64; i < n; i += 32) {
+    for (int i = lane + 32 * RZ; i < n; i += 32) {
       const float4 c = __ldcg(&rz[i]);
       const float sc = expf(-ff_diff(FF{c.x, c.y}, r) * inv_lambda);
       scl[i] = sc;

@@ -521,23 +521,27 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   const int ncol = 2 * T;
   merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.inv_lambda_f, scl,
                  &ts.rho, &ts.Z, col_hi, col_lo, mbuf, tid, nthreads);
-  for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
-  if (tid == 0) {
-    D.gpart_rz[g] = make_float4(ts.rho.hi, ts.rho.lo, ts.Z.hi, ts.Z.lo);
-    D.counters[g] = 0u;
+  if (D.nGroups > 1) {
+    for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
+    if (tid == 0) {
+      D.gpart_rz[g] = make_float4(ts.rho.hi, ts.rho.lo, ts.Z.hi, ts.Z.lo);
+      D.counters[g] = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      unsigned tk = atomicAdd(&D.counters[D.nGroups], 1u);
+      ts.flag = (tk == (unsigned)(D.nGroups - 1));
+      if (ts.flag) __threadfence();
+    }
+    __syncthreads();
+    if (!ts.flag) return;
+    merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z,
+                   col_hi, col_lo, mbuf, tid, nthreads);
+    if (tid == 0) D.counters[D.nGroups] = 0u;
+  } else if (tid == 0) {
+    D.counters[0] = 0u;  // one group: its merge was the final one
   }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    unsigned tk = atomicAdd(&D.counters[D.nGroups], 1u);
-    ts.flag = (tk == (unsigned)(D.nGroups - 1));
-    if (ts.flag) __threadfence();
-  }
-  __syncthreads();
-  if (!ts.flag) return;
-  merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z, col_hi,
-                 col_lo, mbuf, tid, nthreads);
-  if (tid == 0) D.counters[D.nGroups] = 0u;
   final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
 }
 
