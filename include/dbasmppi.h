@@ -43,7 +43,7 @@ extern "C" {
 
 /* Dynamics (Eq. 1).  MPPI_UNICYCLE: state (x, y, theta), control (v, omega),
  * x' = x + v cos(theta) dt, y' = y + v sin(theta) dt, theta' = theta + omega dt.
- * MPPI_QUAD2D: planar quadrotor with the constants of Sec. IV-A, state
+ * MPPI_QUAD2D: planar quadrotor with the constants of Sec. V-A, state
  * (y, z, phi, ydot, zdot, phidot), control (u1, u2) = thrust deviations with
  * F_i = m g / 2 + u_i; explicit Euler with the right-hand side at step k as
  * in Eq. 12. */
@@ -55,9 +55,11 @@ extern "C" {
 #define MPPI_MAX_K (1 << 22)  /* samples */
 #define MPPI_MAX_OBSTACLES 4096
 #define MPPI_MAX_SHAPE 8      /* shape points per body */
+#define MPPI_MAX_COORD 1.0e6  /* |cx|, |cy| and r of an obstacle, metres */
+#define MPPI_MIN_H_EPS 1.0e-18 /* smallest accepted h_eps */
 
 /* Problem parameters.  Names follow the paper: K = M samples, T = N horizon,
- * dt (Sec. IV), lambda the temperature of Eq. 4 (the cost is divided by it),
+ * dt (Sec. V), lambda the temperature of Eq. 4 (the cost is divided by it),
  * Sigma_u the 2x2 sampling covariance, (ln_mu, ln_sigma) the log-normal factor
  * of Eq. 11, mu_coarse the coarseness factor mu of Eq. 10 (<= 0 keeps
  * S_e = 1), gamma_ctrl the control-cost gamma of Eq. 9, gamma_bas the gamma
@@ -104,7 +106,7 @@ typedef struct mppi_ctx mppi_ctx;
  * u_t), or NULL for zeros.  S_e starts at mu ln(e) = mu (Eq. 10 with
  * C_B = 0).  Errors: MPPI_EINVAL (sizes beyond the limits, Sigma_u not
  * symmetric positive semi-definite, Sigma_u singular while gamma_ctrl != 0,
- * lambda <= 0, gamma_bas outside (0,1), h_eps <= 0, u_min > u_max, non-finite
+ * lambda <= 0, gamma_bas outside (0,1), h_eps < MPPI_MIN_H_EPS, u_min > u_max, non-finite
  * values), MPPI_ENOMEM, MPPI_ECUDA. */
 int mppi_create(const mppi_params* p, const double* u_init, mppi_ctx** out);
 
@@ -114,7 +116,8 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init,
 
 /* Replace the obstacle set.  cxcyr: J x 3 (centre x, centre y, radius) in
  * the world frame; copied.  J may be 0 (empty set, barrier sum 0).  Errors:
- * MPPI_EINVAL (J < 0, J > MPPI_MAX_OBSTACLES, non-finite value, radius < 0).
+ * MPPI_EINVAL (J < 0, J > MPPI_MAX_OBSTACLES, non-finite value, radius < 0,
+ * |cx|, |cy| or r above MPPI_MAX_COORD).
  * Synchronises with the context's last stream before replacing the set. */
 int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J);
 

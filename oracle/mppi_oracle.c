@@ -18,7 +18,7 @@
  *   Eq. 4   min-shifted exponentiated weights, update -> orc_weights, orc_step
  *   Eq. 10  S_e = mu log(e + C_B(X*))                  -> orc_step
  *   Eq. 11  NLN product of a normal and a log-normal  -> orc_noise
- *   Eq. 12  planar quadrotor (6-state two-thrust form of Sec. IV-A constants)
+ *   Eq. 12  planar quadrotor (6-state two-thrust form of Sec. V-A constants)
  *   Eq. 13/15 h = |p_i - c_j|^2 - r_j^2 over shape points and obstacles
  *   Alg. 1  the outer-loop body: sample, roll out, weight, update, actuate,
  *           nominal rollout for C_B, S_e, shift.

@@ -44,7 +44,7 @@ int fail(int code, const char* fmt, ...) {
 __global__ void prep_kernel(const __grid_constant__ CtrlDesc D, int init) {
   __shared__ double red[64];
   if (init) init_constants(D, threadIdx.x, blockDim.x);
-  prep_constants(D, D.U, red, threadIdx.x, blockDim.x);
+  prep_constants(D, D.U, &D.st->S_e, red, threadIdx.x, blockDim.x);
 }
 
 __global__ void weights_kernel(const double* __restrict__ costs, int K,
@@ -98,6 +98,16 @@ bool finite_all(const double* a, int n) {
   return true;
 }
 
+// One obstacle (cx, cy, r): finite, r >= 0, and within MPPI_MAX_COORD of the
+// origin (which keeps the barrier's paired products h1 h2 finite in FP32).
+int check_obstacle(const double* o, int j) {
+  if (!finite_all(o, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
+  if (o[2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+  if (std::fabs(o[0]) > MPPI_MAX_COORD || std::fabs(o[1]) > MPPI_MAX_COORD || o[2] > MPPI_MAX_COORD)
+    return fail(MPPI_EINVAL, "obstacle %d lies beyond %g m", j, (double)MPPI_MAX_COORD);
+  return 0;
+}
+
 int validate(const mppi_params* p) {
   if (!p) return fail(MPPI_EINVAL, "params is NULL");
   if (p->model != MPPI_UNICYCLE && p->model != MPPI_QUAD2D)
@@ -116,7 +126,7 @@ int validate(const mppi_params* p) {
   if (!(p->dt > 0)) return fail(MPPI_EINVAL, "dt must be > 0");
   if (!(p->lambda > 0)) return fail(MPPI_EINVAL, "lambda must be > 0");
   if (!(p->gamma_bas > 0 && p->gamma_bas < 1)) return fail(MPPI_EINVAL, "gamma_bas must be in (0,1)");
-  if (!(p->h_eps > 0)) return fail(MPPI_EINVAL, "h_eps must be > 0");
+  if (!(p->h_eps >= MPPI_MIN_H_EPS)) return fail(MPPI_EINVAL, "h_eps must be >= %g", MPPI_MIN_H_EPS);
   if (p->ln_sigma < 0) return fail(MPPI_EINVAL, "ln_sigma must be >= 0");
   for (int d = 0; d < 2; ++d)
     if (p->u_min[d] > p->u_max[d]) return fail(MPPI_EINVAL, "u_min > u_max");
@@ -415,7 +425,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   ALLOC(c->d_part_rz, sizeof(float4) * nTiles);
   ALLOC(c->d_gpart, sizeof(float) * (size_t)nGroups * 2 * T);
   ALLOC(c->d_gpart_rz, sizeof(float4) * nGroups);
-  ALLOC(c->d_cnt, sizeof(unsigned) * (nGroups + 1));
+  ALLOC(c->d_cnt, sizeof(unsigned) * 2 * (nGroups + 1));
   ALLOC(c->d_costs, sizeof(double) * K);
   ALLOC(c->d_coll, K);
   ALLOC(c->d_Ustar, sizeof(double) * 2 * T);
@@ -450,7 +460,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   for (int i = 0; i < 2 * T; ++i) U0[i] = u_init ? u_init[i] : 0.0;
   if (cudaMemcpy(c->d_U, U0, sizeof(double) * 2 * T, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_st, &st, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(c->d_cnt, 0, sizeof(unsigned) * (nGroups + 1)) != cudaSuccess) {
+      cudaMemset(c->d_cnt, 0, sizeof(unsigned) * 2 * (nGroups + 1)) != cudaSuccess) {
     free_ctx(c);
     return fail(MPPI_ECUDA, "initial upload failed");
   }
@@ -473,8 +483,7 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
     return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
   if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
   for (int j = 0; j < J; ++j) {
-    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
-    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+    if (int rc = check_obstacle(cxcyr + 3 * j, j)) return rc;
   }
   mppi_tiling t;
   int smem = 0;
@@ -687,7 +696,7 @@ constexpr int kMaxStaticDevices = 64;
 unsigned char* g_static_base[kMaxStaticDevices] = {nullptr};  // device address, per device
 
 // Device-side copy of the caller's controller state into the scratch state
-// block, ticket counters cleared, constants derived; the caller's ctl is
+// block, ticket counters and minimum words cleared, constants derived; the caller's ctl is
 // {S_e, beta, first, iter, status}.
 __global__ void static_prologue(const __grid_constant__ CtrlDesc D, const double* __restrict__ ctl,
                                 int n_counters) {
@@ -702,7 +711,7 @@ __global__ void static_prologue(const __grid_constant__ CtrlDesc D, const double
   for (int i = threadIdx.x; i < n_counters; i += blockDim.x) D.counters[i] = 0u;
   __syncthreads();
   init_constants(D, threadIdx.x, blockDim.x);
-  prep_constants(D, D.U, red, threadIdx.x, blockDim.x);
+  prep_constants(D, D.U, &D.st->S_e, red, threadIdx.x, blockDim.x);
 }
 
 __global__ void static_epilogue(const DevState* __restrict__ st, double* __restrict__ ctl,
@@ -767,7 +776,7 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   const size_t o_prz = carve(&off, sizeof(float4) * nTiles);
   const size_t o_gpart = carve(&off, sizeof(float) * (size_t)nGroups * 2 * T);
   const size_t o_grz = carve(&off, sizeof(float4) * nGroups);
-  const size_t o_cnt = carve(&off, sizeof(unsigned) * (nGroups + 1));
+  const size_t o_cnt = carve(&off, sizeof(unsigned) * 2 * (nGroups + 1));
   const size_t o_costs = d_costs ? 0 : carve(&off, sizeof(double) * K);
   const size_t o_coll = carve(&off, (size_t)K);
   const size_t o_Ustar = carve(&off, sizeof(double) * 2 * T);
@@ -794,7 +803,7 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   c.D.J = J;
   if (J > 0)
     CK(cudaMemcpyAsync(c.d_obst, d_obst, sizeof(double) * 3 * J, cudaMemcpyDeviceToDevice, s));
-  static_prologue<<<1, 256, 0, s>>>(c.D, d_ctl, nGroups + 1);
+  static_prologue<<<1, 256, 0, s>>>(c.D, d_ctl, 2 * (nGroups + 1));
   CK(cudaGetLastError());
   StepFn fn = pick_kernel(p->model, c.tl.positions_per_thread);
   fn<<<c.D.nTiles, c.tl.threads, c.smem, s>>>(c.D, d_x0, d_xref);
@@ -1003,7 +1012,7 @@ size_t slot_bytes(const mppi_params* p, const mppi_tiling* t, int Jcap) {
   carve(&off, sizeof(float4) * nTiles);
   carve(&off, sizeof(float) * (size_t)nGroups * 2 * T);
   carve(&off, sizeof(float4) * nGroups);
-  carve(&off, sizeof(unsigned) * (nGroups + 1));
+  carve(&off, sizeof(unsigned) * 2 * (nGroups + 1));
   carve(&off, sizeof(double) * K);
   carve(&off, (size_t)K);
   carve(&off, sizeof(double) * 2 * T);
@@ -1028,7 +1037,7 @@ void slot_layout(mppi_batch* b, BatchSlot& s, mppi_ctx* c) {
   c->d_part_rz = (float4*)(base + carve(&off, sizeof(float4) * nTiles));
   c->d_gpart = (float*)(base + carve(&off, sizeof(float) * (size_t)nGroups * 2 * T));
   c->d_gpart_rz = (float4*)(base + carve(&off, sizeof(float4) * nGroups));
-  c->d_cnt = (unsigned*)(base + carve(&off, sizeof(unsigned) * (nGroups + 1)));
+  c->d_cnt = (unsigned*)(base + carve(&off, sizeof(unsigned) * 2 * (nGroups + 1)));
   c->d_costs = (double*)(base + carve(&off, sizeof(double) * K));
   c->d_coll = (uint8_t*)(base + carve(&off, (size_t)K));
   c->d_Ustar = (double*)(base + carve(&off, sizeof(double) * 2 * T));
@@ -1107,8 +1116,7 @@ int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
     return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
   if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
   for (int j = 0; j < J; ++j) {
-    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
-    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+    if (int rc = check_obstacle(cxcyr + 3 * j, j)) return rc;
   }
   int slot = -1;
   for (int i = 0; i < b->max_ctrl; ++i)
@@ -1154,7 +1162,7 @@ int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
   const int nGroups = s.D.nGroups;
   bool up = cudaMemcpy(s.D.U, U.data(), sizeof(double) * 2 * p->T, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(s.D.st, &st, sizeof(DevState), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemset(s.D.counters, 0, sizeof(unsigned) * (nGroups + 1)) == cudaSuccess;
+            cudaMemset(s.D.counters, 0, sizeof(unsigned) * 2 * (nGroups + 1)) == cudaSuccess;
   if (up && J > 0)
     up = cudaMemset(b->pool + s.obst_off, 0, (size_t)align_up(24 * J, 16)) == cudaSuccess &&
          cudaMemcpy(b->pool + s.obst_off, cxcyr, sizeof(double) * 3 * J, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -1183,8 +1191,7 @@ int mppi_batch_set_obstacles(mppi_batch* b, int32_t slot, const double* cxcyr, i
     return fail(MPPI_EINVAL, "J=%d out of [0, %d]", J, MPPI_MAX_OBSTACLES);
   if (J > 0 && !cxcyr) return fail(MPPI_EINVAL, "obstacles pointer is NULL");
   for (int j = 0; j < J; ++j) {
-    if (!finite_all(cxcyr + 3 * j, 3)) return fail(MPPI_EINVAL, "obstacle %d is not finite", j);
-    if (cxcyr[3 * j + 2] < 0) return fail(MPPI_EINVAL, "obstacle %d has a negative radius", j);
+    if (int rc = check_obstacle(cxcyr + 3 * j, j)) return rc;
   }
   BatchSlot& s = b->slots[slot];
   mppi_tiling t;

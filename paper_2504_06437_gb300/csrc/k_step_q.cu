@@ -3,13 +3,13 @@
 
 namespace dbm {
 
-__global__ void __launch_bounds__(512) step_q8(const __grid_constant__ CtrlDesc D,
+__global__ void __maxnreg__(DBM_STEP_MAXNREG) step_q8(const __grid_constant__ CtrlDesc D,
                                                 const double* __restrict__ x0,
                                                 const double* __restrict__ xref) {
   step_body<1, 8>(D, x0, xref);
 }
 
-__global__ void __launch_bounds__(512) step_q14(const __grid_constant__ CtrlDesc D,
+__global__ void __maxnreg__(DBM_STEP_MAXNREG) step_q14(const __grid_constant__ CtrlDesc D,
                                                  const double* __restrict__ x0,
                                                  const double* __restrict__ xref) {
   step_body<1, 14>(D, x0, xref);

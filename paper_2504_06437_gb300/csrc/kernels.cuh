@@ -7,6 +7,14 @@
 
 namespace dbm {
 
+// Register cap of the one-controller step kernels: 96 lets five 128-thread
+// CTAs (20 warps) share an SM where the uncapped allocation fits four.  The
+// merge and the final stage, which run once per launch, are what would
+// otherwise raise the kernel's allocation.
+#ifndef DBM_STEP_MAXNREG
+#define DBM_STEP_MAXNREG 96
+#endif
+
 // One step of one controller: one CTA per tile (MODEL: 0 unicycle,
 // 1 planar quadrotor; 8 or 14 world points per barrier thread).
 __global__ void step_u8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,

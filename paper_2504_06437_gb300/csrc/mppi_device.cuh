@@ -83,7 +83,7 @@ struct CtrlDesc {
   uint32_t key0, key1;
   double* U;                 // T x 2 nominal sequence
   float2* cU;                // T: U in FP32 for the next step
-  float2* cA;                // T: gamma (S_e Sigma)^-1 u_t in FP32
+  float2* cA;                // T: gamma Sigma^-1 u_t in FP32 (divided by S_e where used)
   float* cw;                 // T: R_B c_{t+1}, weight of step t's barrier sum
   DevState* st;
   const double* obst;        // J x 3 (cx, cy, r), padded to 16 bytes
@@ -93,7 +93,7 @@ struct CtrlDesc {
   float4* part_rz;           // nTiles x (rho_c hi, lo, Z_c hi, lo), rho relative to base
   float* gpart;              // nGroups x 2T
   float4* gpart_rz;          // nGroups
-  unsigned* counters;        // nGroups + 1 tickets (zero between steps)
+  unsigned* counters;        // 2 (nGroups + 1): tickets, then minimum words (zero between steps)
   double* costs;             // K
   uint8_t* coll;             // K
   double* Ustar;             // T x 2
@@ -111,6 +111,21 @@ struct SmemLayout {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Tile merge geometry (merge_partials): row groups over the CTA's threads
+// and the bytes of their float-pair column sums.
+constexpr int kMergeLoads = 16;   // float2 loads in flight per thread
+constexpr int kMergeGroups = 32;  // row groups at most
+__host__ __device__ inline int merge_row_groups(int ncol, int nthreads) {
+  const int ncp = ncol / 2;
+  int rg = ncp > 0 ? nthreads / ncp : nthreads;
+  if (rg < 1) rg = 1;
+  if (rg > kMergeGroups) rg = kMergeGroups;
+  return rg;
+}
+__host__ __device__ inline int merge_buf_bytes(int ncol, int nthreads) {
+  return align_up(8 * merge_row_groups(ncol, nthreads) * (ncol + 1), 16);  // + Z
+}
+
 __host__ __device__ inline SmemLayout smem_layout(int T, int S, int P, int J, int n, int nscl,
                                                   int nwarps) {
   SmemLayout L;
@@ -122,7 +137,7 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int P, int J, in
   int main_b = 16 * T * S + 8 * T * S;
   int raw_b = align_up(24 * J, 16);
   int nom_b = 16 * T + 4 * T * P;
-  int merge_b = 8 * 2 * T * nwarps;
+  int merge_b = merge_buf_bytes(2 * T, 32 * nwarps) + 8 * (nscl > 1 ? nscl : 1);
   int reg = main_b;
   if (raw_b > reg) reg = raw_b;
   if (nom_b > reg) reg = nom_b;
@@ -325,13 +340,17 @@ struct TileScratch {
   int flag;
   double beta0, beta_d, Kconst, base;  // base = C0 + Kconst
   FF rho, Z;                           // merge results
+  float ref;                           // common reference of a merge (minimum of the sources' rho)
+  double S_e_used, S_e_next;           // exploration rate of this step and the next
+  unsigned long long iter;             // iteration counter of this step
 };
 
 // Fused barrier over nunits (step, sample) units; unit u has pose pose[u]
 // and P shape points shp[0..P).  Each thread takes NPOS / P whole units at a
 // time (NPOS >= P), keeps their world points in registers and streams every
 // obstacle: h = |p - c|^2 - r^2 evaluated as fma(dx, dx, fma(dy, dy, -r^2)),
-// term 1 / max(h, h_eps) by the approximate reciprocal.  A unit's points are
+// terms 1 / max(h, h_eps) added two obstacles at a time as (h1 + h2) / (h1 h2)
+// with the approximate reciprocal.  A unit's points are
 // summed exactly (TwoSum) into (hi, lo), stored at uB[u * ustride]; the sign
 // bit of hi marks a unit in which some h <= 0 (collision).  A thread reads
 // the poses of its units before it writes their sums, so uB may overlay
@@ -361,13 +380,31 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
         ++uu;
       }
     }
-    for (int j = 0; j < J; ++j) {
+    // obstacles in pairs: 1/h1 + 1/h2 = (h1 + h2) / (h1 h2), one reciprocal
+    // for two terms (h1 h2 stays finite for |p - c| < 4e9 m and h_eps >= 1e-18);
+    // with more points per thread the pair's temporaries would not fit
+    int j = 0;
+    if constexpr (NPOS <= 8)
+    for (; j + 1 < J; j += 2) {
+      const float4 o = obs4[j], q = obs4[j + 1];
+#pragma unroll
+      for (int i = 0; i < NPOS; ++i) {
+        const float dx = X[i] - o.x, dy = Y[i] - o.y;
+        const float ex = X[i] - q.x, ey = Y[i] - q.y;
+        float h1 = fmaf(dx, dx, fmaf(dy, dy, o.z));
+        float h2 = fmaf(ex, ex, fmaf(ey, ey, q.z));
+        mn[i] = fminf(mn[i], fminf(h1, h2));
+        h1 = fmaxf(h1, h_eps);
+        h2 = fmaxf(h2, h_eps);
+        acc[i] = fmaf(h1 + h2, rcp_approx(h1 * h2), acc[i]);
+      }
+    }
+    for (; j < J; ++j) {
       const float4 o = obs4[j];
 #pragma unroll
       for (int i = 0; i < NPOS; ++i) {
-        float dx = X[i] - o.x;
-        float dy = Y[i] - o.y;
-        float h = fmaf(dx, dx, fmaf(dy, dy, o.z));
+        const float dx = X[i] - o.x, dy = Y[i] - o.y;
+        const float h = fmaf(dx, dx, fmaf(dy, dy, o.z));
         mn[i] = fminf(mn[i], h);
         acc[i] += rcp_approx(fmaxf(h, h_eps));
       }
@@ -415,123 +452,92 @@ __device__ __forceinline__ FF warp_sum_ff(FF a) {
   return a;
 }
 
-// Merge n partial results (rho_i, Z_i, cols_i[ncol]) taken relative to their
-// own minima into one relative to the common minimum: the log-sum-exp merge
-// of Eq. 4's numerator and denominator.  Warp w takes sources w, w + nwarps,
-// ...; lane l takes columns l, l + 32, ... (ncol <= 32 * kMaxColsPerLane).
-// Every load (the sources' minima and normalisers, and batches of whole rows)
-// is issued before the first value is used, so the merge costs about one
-// round trip to L2 per batch; the per-warp float-pair sums are then added in
-// warp order.  The normaliser is summed as a float pair.  All threads of the
-// CTA call it.  buf: nwarps x ncol float pairs.  Outputs in shared memory:
-// *rho_out, *Z_out, col_hi/col_lo[ncol].
-constexpr int kMaxColsPerLane = 16;  // 2 T <= 512
-constexpr int kMergeLoads = 32;      // loads in flight per lane
-template <int NJ>  // column slots per lane: ncol <= 32 NJ
-__device__ inline void merge_partials_nj(int n, const float4* rz, const float* cols, int ncol,
-                                         float inv_lambda, float* scl, FF* rho_out, FF* Z_out,
-                                         float* col_hi, float* col_lo, FF* buf, int tid,
-                                         int nthreads) {
-  constexpr int RPB = kMergeLoads / NJ;  // rows per batch per warp
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
-  float v[kMergeLoads];
-  int i0 = warp;
-  auto load_batch = [&](int first) {
-#pragma unroll
-    for (int q = 0; q < kMergeLoads; ++q) {
-      const int r = q / NJ, j = q % NJ;
-      const int i = first + r * nwarps;
-      const int c = lane + 32 * j;
-      v[q] = (i < n && c < ncol) ? __ldcg(cols + (size_t)i * ncol + c) : 0.0f;
-    }
-  };
-  load_batch(i0);  // issued before the minima are known
-  if (warp == 0) {
-    // all (rho_i, Z_i) of this lane's sources in flight at once
-    constexpr int RZ = 4;
-    const float inf = __int_as_float(0x7f800000);
-    float4 rr[RZ];
-#pragma unroll
-    for (int q = 0; q < RZ; ++q) {
-      const int i = lane + 32 * q;
-      rr[q] = i < n ? __ldcg(&rz[i]) : make_float4(inf, 0.0f, 0.0f, 0.0f);
-    }
-    FF r = FF{rr[0].x, rr[0].y};
-#pragma unroll
-    for (int q = 1; q < RZ; ++q)
-      if (ff_less(FF{rr[q].x, rr[q].y}, r)) r = FF{rr[q].x, rr[q].y};
-    for (int i = lane + 32 * RZ; i < n; i += 32) {
-      const float4 c = __ldcg(&rz[i]);
-      if (ff_less(FF{c.x, c.y}, r)) r = FF{c.x, c.y};
-    }
-    r = warp_min_ff(r);
-    FF z = {0.0f, 0.0f};
-#pragma unroll
-    for (int q = 0; q < RZ; ++q) {
-      const int i = lane + 32 * q;
-      if (i < n) {
-        const float sc = expf(-ff_diff(FF{rr[q].x, rr[q].y}, r) * inv_lambda);
-        scl[i] = sc;
-        ff_add_prod(z, sc, rr[q].z, rr[q].w);
-      }
-    }
-    for (int i = lane + 32 * RZ; i < n; i += 32) {
-      const float4 c = __ldcg(&rz[i]);
-      const float sc = expf(-ff_diff(FF{c.x, c.y}, r) * inv_lambda);
-      scl[i] = sc;
-      ff_add_prod(z, sc, c.z, c.w);
-    }
-    z = warp_sum_ff(z);
-    if (lane == 0) {
-      *rho_out = r;
-      *Z_out = ff_norm(z);
-    }
-  }
-  __syncthreads();
-  FF acc[NJ];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) acc[j].hi = acc[j].lo = 0.0f;
-  for (;;) {
-#pragma unroll
-    for (int q = 0; q < kMergeLoads; ++q) {
-      const int r = q / NJ, j = q % NJ;
-      const int i = i0 + r * nwarps;
-      if (i < n) ff_add(acc[j], v[q] * scl[i]);
-    }
-    i0 += RPB * nwarps;
-    if (i0 >= n) break;
-    load_batch(i0);
-  }
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int c = lane + 32 * j;
-    if (c < ncol) buf[warp * ncol + c] = acc[j];
-  }
-  __syncthreads();
-  for (int c = tid; c < ncol; c += nthreads) {
-    FF a = buf[c];
-    for (int w = 1; w < nwarps; ++w) a = ff_sum(a, buf[w * ncol + c]);
-    col_hi[c] = a.hi;
-    col_lo[c] = a.lo;
-  }
-  __syncthreads();
+// Minimum of floats by an integer atomic: key(f) = ~u(f), u the
+// order-preserving unsigned image of f, so that a larger key is a smaller f
+// and 0 (the cleared word) is below every key of a number.  atomicMax over
+// keys is an exact, order-independent minimum.
+__device__ __forceinline__ unsigned min_key(float f) {
+  const int i = __float_as_int(f);
+  return ~((unsigned)(i >= 0 ? i : i ^ 0x7fffffff) ^ 0x80000000u);
+}
+__device__ __forceinline__ float key_min(unsigned k) {
+  const int i = (int)(~k ^ 0x80000000u);
+  return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
 }
 
+// Merge n partial results (rho_i, Z_i, cols_i[ncol]), each taken relative to
+// its own minimum rho_i, into one relative to ref = min_i rho_i.hi: the
+// log-sum-exp merge of Eq. 4's numerator and denominator.  Source i is scaled
+// by s_i = exp(-(rho_i - ref) / lambda) <= 1 (thread i computes it while the
+// column loads are in flight).  The ncol columns are read as ncp = ncol / 2
+// float pairs: thread tid takes the cell (row group rg, column pair cp) =
+// (tid / ncp, tid % ncp), i.e. rows rg, rg + RG, ... of that pair, up to
+// kMergeLoads rows in flight; the threads with cp = 0 also add s_i Z_i.  The
+// row groups are then added in order.  All threads of the CTA call it.
+// Shared memory: scl (n floats), zi (n float2), buf (merge_buf_bytes).
+// Outputs in shared memory: *Z_out, col_hi/col_lo[ncol].
 __device__ inline void merge_partials(int n, const float4* rz, const float* cols, int ncol,
-                                      float inv_lambda, float* scl, FF* rho_out, FF* Z_out,
-                                      float* col_hi, float* col_lo, FF* buf, int tid,
+                                      float ref, float inv_lambda, float* scl, float2* zi, FF* buf,
+                                      FF* Z_out, float* col_hi, float* col_lo, int tid,
                                       int nthreads) {
-  const int nj = (ncol + 31) / 32;
-  if (nj <= 1)
-    merge_partials_nj<1>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
-  else if (nj <= 2)
-    merge_partials_nj<2>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
-  else if (nj <= 4)
-    merge_partials_nj<4>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
-  else if (nj <= 8)
-    merge_partials_nj<8>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
-  else
-    merge_partials_nj<16>(n, rz, cols, ncol, inv_lambda, scl, rho_out, Z_out, col_hi, col_lo, buf, tid, nthreads);
+  const int ncp = ncol >> 1;
+  const int RG = merge_row_groups(ncol, nthreads);
+  const int ncell = RG * ncp;
+  const int ldb = ncol + 1;  // buf row: the columns, then Z
+  const float2* cols2 = reinterpret_cast<const float2*>(cols);
+  float2 v[kMergeLoads];
+  auto load = [&](int cell, int r0) {
+    const int rg = cell / ncp, cp = cell - rg * ncp;
+#pragma unroll
+    for (int q = 0; q < kMergeLoads; ++q) {
+      const int i = rg + (r0 + q) * RG;
+      v[q] = (cell < ncell && i < n) ? __ldcg(cols2 + (size_t)i * ncp + cp) : make_float2(0.0f, 0.0f);
+    }
+  };
+  load(tid, 0);
+  for (int i = tid; i < n; i += nthreads) {
+    const float4 c = __ldcg(rz + i);
+    scl[i] = expf(-((c.x - ref) + c.y) * inv_lambda);
+    zi[i] = make_float2(c.z, c.w);
+  }
+  __syncthreads();
+  for (int cell = tid; cell < ncell; cell += nthreads) {
+    const int rg = cell / ncp, cp = cell - rg * ncp;
+    FF a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, z = {0.0f, 0.0f};
+    for (int r0 = 0;; r0 += kMergeLoads) {
+#pragma unroll
+      for (int q = 0; q < kMergeLoads; ++q) {
+        const int i = rg + (r0 + q) * RG;
+        if (i < n) {
+          const float sc = scl[i];
+          ff_add(a0, v[q].x * sc);
+          ff_add(a1, v[q].y * sc);
+          if (cp == 0) {
+            const float2 zz = zi[i];
+            ff_add_prod(z, sc, zz.x, zz.y);
+          }
+        }
+      }
+      if (rg + (r0 + kMergeLoads) * RG >= n) break;
+      load(cell, r0 + kMergeLoads);
+    }
+    buf[rg * ldb + 2 * cp] = a0;
+    buf[rg * ldb + 2 * cp + 1] = a1;
+    if (cp == 0) buf[rg * ldb + ncol] = z;
+    if (cell + nthreads < ncell) load(cell + nthreads, 0);
+  }
+  __syncthreads();
+  for (int c = tid; c <= ncol; c += nthreads) {
+    FF a = buf[c];
+    for (int g = 1; g < RG; ++g) a = ff_sum(a, buf[g * ldb + c]);
+    if (c < ncol) {
+      col_hi[c] = a.hi;
+      col_lo[c] = a.lo;
+    } else {
+      *Z_out = ff_norm(a);
+    }
+  }
+  __syncthreads();
 }
 
 // Fused barrier over npos positions, one position per thread at a time

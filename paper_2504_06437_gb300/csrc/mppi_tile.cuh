@@ -32,20 +32,20 @@ __device__ inline void init_constants(const CtrlDesc& D, int tid, int nthreads) 
   }
 }
 
-// Per-step constants that depend only on the controller state (U, S_e):
-// chol(S_e Sigma) = sqrt(S_e) chol(Sigma), a_t = gamma (S_e Sigma)^-1 u_t
-// = (gamma Sigma^-1 / S_e) u_t, u_t in FP32, and C0 = sum_t u_t . a_t, the
-// part of the control cost of Eq. 9 (Algorithm 1 form
-// gamma u^T (S_e Sigma)^-1 v) that every sample shares.  Run by one CTA after
-// each shift, and by a one-CTA kernel after the host sets the state.
-// Usrc: the sequence (shared or global memory); red: >= 32 doubles of shared
-// memory.
-__device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, double* red, int tid,
-                                      int nthreads) {
+// Per-step constants that depend only on the controller state (U, S_e), for
+// a state the host has set: chol(S_e Sigma) = sqrt(S_e) chol(Sigma), u_t in
+// FP32, a'_t = gamma Sigma^-1 u_t (the step divides it by S_e: a_t = gamma
+// (S_e Sigma)^-1 u_t) and C0 = sum_t u_t . a_t, the part of the control cost
+// of Eq. 9 (Algorithm 1 form gamma u^T (S_e Sigma)^-1 v) that every sample
+// shares.  The final stage forms the same constants after each shift.
+// Usrc: the sequence; Se_src: S_e, read after the first barrier; red: >= 32
+// doubles of shared memory.
+__device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, const double* Se_src,
+                                      double* red, int tid, int nthreads) {
   DevState* st = D.st;
   const int T = D.T;
   __syncthreads();
-  const float Se = (float)st->S_e;
+  const float Se = (float)*Se_src;
   const float inv_Se = 1.0f / Se;
   if (tid == 0) {
     const float r = sqrtf(Se);
@@ -53,8 +53,8 @@ __device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, dou
     st->L10 = r * (float)D.Lsig[1];
     st->L11 = r * (float)D.Lsig[2];
   }
-  const float M00 = (float)D.Sinv[0] * inv_Se, M01 = (float)D.Sinv[1] * inv_Se;
-  const float M10 = (float)D.Sinv[2] * inv_Se, M11 = (float)D.Sinv[3] * inv_Se;
+  const float M00 = (float)D.Sinv[0], M01 = (float)D.Sinv[1];
+  const float M10 = (float)D.Sinv[2], M11 = (float)D.Sinv[3];
   FF c0 = {0.0f, 0.0f};
   for (int t = tid; t < T; t += nthreads) {
     const float u0 = (float)Usrc[2 * t], u1 = (float)Usrc[2 * t + 1];
@@ -71,10 +71,10 @@ __device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, dou
     redf[2 * (tid >> 5) + 1] = c0.lo;
   }
   __syncthreads();
-  if (tid == 0) {
-    FF sum = {0.0f, 0.0f};
-    for (int w = 0; w < (nthreads >> 5); ++w) sum = ff_sum(sum, FF{redf[2 * w], redf[2 * w + 1]});
-    st->C0 = (double)sum.hi + (double)sum.lo;
+  if (tid < 32) {
+    FF sum = tid < (nthreads >> 5) ? FF{redf[2 * tid], redf[2 * tid + 1]} : FF{0.0f, 0.0f};
+    sum = warp_sum_ff(sum);
+    if (tid == 0) st->C0 = (double)((sum.hi + sum.lo) * inv_Se);
   }
   __syncthreads();
 }
@@ -90,7 +90,8 @@ __device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, dou
 // pose after step t is written to pose[t * ps] as (x, y, cos, sin) of the
 // heading.  With COST the lane also adds to `cost` its steps' stage cost
 // q(x_{t+1}) and control cost a_t . (v_t - u_t) of Eq. 9 (Algorithm 1 form,
-// the sample-independent part u_t . a_t excluded), and phi(x_T).
+// the sample-independent part u_t . a_t excluded), and phi(x_T): summed in
+// FP32 over the lane's ceil(T / 32) steps, then added to the float pair once.
 template <int MODEL, bool COST>
 __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int vs,
                                 const float* __restrict__ x_init, float4* pose, int ps,
@@ -102,6 +103,7 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
     float cth = x_init[2], cx = x_init[0], cy = x_init[1];
     float cs_, cc_;
     sincosf(cth, &cs_, &cc_);
+    float lc = 0.0f;  // this lane's few stage terms, in FP32
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;
       const bool valid = t < T;
@@ -123,13 +125,13 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
         if constexpr (COST) {
           const float* xr = xrf + (t + 1) * 3;
           const float e0 = xa - xr[0], e1 = ya - xr[1], e2 = th_a - xr[2];
-          ff_add(cost, fmaf(D.Q[0] * e0, e0, fmaf(D.Q[1] * e1, e1, D.Q[2] * e2 * e2)));
           const float2 u = Uf[t], a = Af[t];
-          ff_add(cost, fmaf(a.x, v.x - u.x, a.y * (v.y - u.y)));
+          lc += fmaf(D.Q[0] * e0, e0, fmaf(D.Q[1] * e1, e1, fmaf(D.Q[2] * e2, e2,
+                     fmaf(a.x, v.x - u.x, a.y * (v.y - u.y)))));
           if (t == T - 1) {
             const float* xT = xrf + T * 3;
             const float f0 = xa - xT[0], f1 = ya - xT[1], f2 = th_a - xT[2];
-            ff_add(cost, fmaf(D.Qf[0] * f0, f0, fmaf(D.Qf[1] * f1, f1, D.Qf[2] * f2 * f2)));
+            lc += fmaf(D.Qf[0] * f0, f0, fmaf(D.Qf[1] * f1, f1, D.Qf[2] * f2 * f2));
           }
         }
       }
@@ -139,12 +141,14 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
       cx = lane31(xa);
       cy = lane31(ya);
     }
+    if constexpr (COST) ff_add(cost, lc);
   } else {
     float cy = x_init[0], cz = x_init[1], cph = x_init[2];
     float cvy = x_init[3], cvz = x_init[4], cw = x_init[5];
     float cs_, cc_;
     sincosf(cph, &cs_, &cc_);
     const float kw = D.arm_over_I * dt;
+    float lc = 0.0f;
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;
       const bool valid = t < T;
@@ -180,9 +184,8 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
             const float e = xs[d] - xr[d];
             q = fmaf(D.Q[d] * e, e, q);
           }
-          ff_add(cost, q);
           const float2 u = Uf[t], a = Af[t];
-          ff_add(cost, fmaf(a.x, v.x - u.x, a.y * (v.y - u.y)));
+          lc += fmaf(a.x, v.x - u.x, fmaf(a.y, v.y - u.y, q));
           if (t == T - 1) {
             const float* xT = xrf + T * 6;
             float f = 0.0f;
@@ -191,7 +194,7 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
               const float e = xs[d] - xT[d];
               f = fmaf(D.Qf[d] * e, e, f);
             }
-            ff_add(cost, f);
+            lc += f;
           }
         }
       }
@@ -204,18 +207,24 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
       cy = lane31(y_a);
       cz = lane31(z_a);
     }
+    if constexpr (COST) ff_add(cost, lc);
   }
 }
 
 // Final stage (one CTA per controller per step): U* from the merged sums
-// (Eq. 4), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"),
-// S_e (Eq. 10, C_B floored at 0 inside the logarithm), shift, state update.
+// (Eq. 4), the shift (Algorithm 1, last loop: u_t <- u*_{t+1}, the last entry
+// kept), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"), S_e
+// (Eq. 10, C_B floored at 0 inside the logarithm) and the state update.  The
+// next step's constants that do not depend on S_e (u_t in FP32, a'_t = gamma
+// Sigma^-1 u_t and sum_t u_t . a'_t) are formed in the same pass as U* and
+// the shift, one step per thread; S_e enters afterwards through L, C0 and
+// the 1 / S_e that the next step applies to a'_t.
 template <int MODEL, int NPOS>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
                             const double* __restrict__ x0g, double* out) {
-  const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31;
+  const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int T = D.T, P = D.P;
-  double* Us = reinterpret_cast<double*>(smem + L.Us);
+  const double* Us = reinterpret_cast<const double*>(smem + L.Us);  // the step's U
   float2* Usf = reinterpret_cast<float2*>(smem + L.Usf);
   const float* col_hi = reinterpret_cast<const float*>(smem + L.colhi);
   const float* col_lo = reinterpret_cast<const float*>(smem + L.collo);
@@ -225,16 +234,41 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
   const float4* obs4 = reinterpret_cast<const float4*>(smem + L.obs4);
   const float* cw = reinterpret_cast<const float*>(smem + L.cw);
   const float* xi = reinterpret_cast<const float*>(smem + L.xi);
-  const double Z = (double)ts.Z.hi + (double)ts.Z.lo;
-  const double invZ = 1.0 / Z;
-  for (int c = tid; c < 2 * T; c += nthreads) {
-    int d = c & 1;
-    double du = ((double)col_hi[c] + (double)col_lo[c]) * invZ;
-    double u = Us[c] + du;  // Us holds the step's U, prefetched by the prologue
-    u = fmin(fmax(u, D.umin_d[d]), D.umax_d[d]);
-    Us[c] = u;
-    reinterpret_cast<float*>(Usf)[c] = (float)u;
-    D.Ustar[c] = u;
+  float* redf = reinterpret_cast<float*>(smem + L.red);
+  // Z >= 1 (the minimum's own weight is 1), so its float reciprocal and the
+  // float quotient carry the update to about 1e-7 relative
+  const float invZ = 1.0f / (ts.Z.hi + ts.Z.lo);
+  const float M00 = (float)D.Sinv[0], M01 = (float)D.Sinv[1];
+  const float M10 = (float)D.Sinv[2], M11 = (float)D.Sinv[3];
+  FF c0 = {0.0f, 0.0f};
+  double us0[2] = {0.0, 0.0};  // u*_0, kept by thread 0
+  for (int t = tid; t < T; t += nthreads) {
+    const int tn = t + 1 < T ? t + 1 : T - 1;
+    double us[2], un[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int c = 2 * t + d, cn = 2 * tn + d;
+      us[d] = fmin(fmax(Us[c] + (double)((col_hi[c] + col_lo[c]) * invZ), D.umin_d[d]), D.umax_d[d]);
+      un[d] = fmin(fmax(Us[cn] + (double)((col_hi[cn] + col_lo[cn]) * invZ), D.umin_d[d]), D.umax_d[d]);
+      D.Ustar[c] = us[d];
+      D.U[c] = un[d];
+    }
+    if (t == 0) {
+      us0[0] = us[0];
+      us0[1] = us[1];
+    }
+    Usf[t] = make_float2((float)us[0], (float)us[1]);
+    const float v0 = (float)un[0], v1 = (float)un[1];
+    const float a0 = fmaf(M00, v0, M01 * v1), a1 = fmaf(M10, v0, M11 * v1);
+    D.cU[t] = make_float2(v0, v1);
+    D.cA[t] = make_float2(a0, a1);
+    ff_add_prod(c0, v0, a0, 0.0f);
+    ff_add_prod(c0, v1, a1, 0.0f);
+  }
+  c0 = warp_sum_ff(c0);
+  if (lane == 0) {
+    redf[2 * warp] = c0.hi;
+    redf[2 * warp + 1] = c0.lo;
   }
   __syncthreads();
   float* x1 = reinterpret_cast<float*>(smem + L.scH);  // per-sample sums are consumed
@@ -249,26 +283,32 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
   if (tid < 32) {
     FF a = {0.0f, 0.0f};
     for (int t = lane; t < T; t += 32) {
-      FF b = {0.0f, 0.0f};
-      for (int p = 0; p < P; ++p) ff_add(b, fabsf(b_nom[t * P + p]));
-      ff_add_prod(a, cw[t], b.hi, b.lo);
+      float b = 0.0f;  // the step's P shape-point sums
+      for (int p = 0; p < P; ++p) b += fabsf(b_nom[t * P + p]);
+      ff_add_prod(a, cw[t], b, 0.0f);
     }
     a = warp_sum_ff(a);
-    const double CB = (double)a.hi + (double)a.lo + ts.Kconst;
+    FF cs = lane < (nthreads >> 5) ? FF{redf[2 * lane], redf[2 * lane + 1]} : FF{0.0f, 0.0f};
+    cs = warp_sum_ff(cs);
     if (tid == 0) {
       DevState* st = D.st;
-      const double S_e_used = st->S_e;
+      const double CB = (double)a.hi + (double)a.lo + ts.Kconst;
       // Eq. 10, C_B floored at 0 inside the logarithm
       const float arg = (float)(2.718281828459045 + fmax(CB, 0.0));
       const double S_e_next = D.mu_coarse > 0.0 ? D.mu_coarse * (double)logf(arg) : 1.0;
+      const float Se = (float)S_e_next, r = sqrtf(Se), inv_Se = 1.0f / Se;
+      st->L00 = r * (float)D.Lsig[0];
+      st->L10 = r * (float)D.Lsig[1];
+      st->L11 = r * (float)D.Lsig[2];
+      st->C0 = (double)((cs.hi + cs.lo) * inv_Se);
       st->rho = ts.base + ((double)ts.rho.hi + (double)ts.rho.lo);
-      st->Z = Z;
+      st->Z = (double)ts.Z.hi + (double)ts.Z.lo;
       st->CB_star = CB;
       st->beta_used = ts.beta0;
       st->beta_d = ts.beta_d;
-      st->S_e_used = S_e_used;
-      st->u0[0] = Us[0];
-      st->u0[1] = Us[1];
+      st->S_e_used = ts.S_e_used;
+      st->u0[0] = us0[0];
+      st->u0[1] = us0[1];
       constexpr int n = Dyn<MODEL>::n;
       double xn[6] = {0, 0, 0, 0, 0, 0};
       xn[0] = x0g[0] + (double)x1[0];  // back from the frame centred on x0
@@ -276,25 +316,16 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       for (int d = 2; d < n; ++d) xn[d] = (double)x1[d];
       for (int d = 0; d < 6; ++d) st->x1[d] = xn[d];
       if (out) {  // batched launches: u0 then the predicted state, 8 doubles
-        out[0] = Us[0];
-        out[1] = Us[1];
+        out[0] = us0[0];
+        out[1] = us0[1];
         for (int d = 0; d < 6; ++d) out[2 + d] = xn[d];
       }
       st->S_e = S_e_next;
       st->beta = ts.beta0;
       st->first = 0;
-      st->iter = st->iter + 1ull;
+      st->iter = ts.iter + 1ull;
     }
   }
-  // shift (Algorithm 1, last loop): u_{t-1} <- u*_t, the last entry kept
-  double* Ush = reinterpret_cast<double*>(smem + L.colhi);  // column sums are consumed
-  for (int c = tid; c < 2 * T; c += nthreads) {
-    int t = c >> 1, d = c & 1;
-    const double u = (t + 1 < T) ? Us[2 * (t + 1) + d] : Us[2 * (T - 1) + d];
-    D.U[c] = u;
-    Ush[c] = u;
-  }
-  prep_constants(D, Ush, reinterpret_cast<double*>(smem + L.red), tid, nthreads);
 }
 
 // One tile of one controller.  ts.mbar must be initialised; mbar_phase is
@@ -328,6 +359,10 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
 
   // ---- prologue: stage obstacles (TMA bulk copy), per-step constants
   __syncthreads();  // previous use of shared memory by this CTA is over
+  if (tid == 0) {  // read early: only the final stage uses them
+    ts.S_e_used = st->S_e;
+    ts.iter = st->iter;
+  }
 #if DBM_STAGE_TMA
   if (tid == 0 && J > 0)
     tma_bulk_g2s(smem + L.region, D.obst, (uint32_t)align_up(24 * J, 16), &ts.mbar);
@@ -336,9 +371,11 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   const double ox = x0g[0], oy = x0g[1];
   if (tid < n) xi[tid] = tid < 2 ? 0.0f : (float)x0g[tid];
   double* Us = reinterpret_cast<double*>(smem + L.Us);
+  const float inv_Se = 1.0f / (float)st->S_e;  // a_t = a'_t / S_e
   for (int t = tid; t < T; t += nthreads) {
     Uf[t] = D.cU[t];
-    Af[t] = D.cA[t];
+    const float2 a = D.cA[t];
+    Af[t] = make_float2(a.x * inv_Se, a.y * inv_Se);
     cw[t] = D.cw[t];
     Us[2 * t] = D.U[2 * t];  // for the final stage, should this CTA run it
     Us[2 * t + 1] = D.U[2 * t + 1];
@@ -480,7 +517,10 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     const float e = valid ? expf(-ff_diff(Sk, rho_c) * D.inv_lambda_f) : 0.0f;
     const FF z = ff_norm(warp_sum_ff(FF{e, 0.0f}));
     eS[lane] = e;
-    if (lane == 0) D.part_rz[tile] = make_float4(rho_c.hi, rho_c.lo, z.hi, z.lo);
+    if (lane == 0) {
+      D.part_rz[tile] = make_float4(rho_c.hi, rho_c.lo, z.hi, z.lo);
+      atomicMax(&D.counters[D.nGroups + 1 + tile / D.GT], min_key(rho_c.hi));
+    }
     if (valid) {
       D.costs[k0 + lane] = ts.base + ((double)Sk.hi + (double)Sk.lo);
       D.coll[k0 + lane] = collf[lane];
@@ -488,60 +528,72 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   }
   __syncthreads();
   {
+    // one thread per column (t, d): sum over the tile's samples, whose
+    // weights eS are zero past K
     float* prow = D.part + (size_t)tile * 2 * T;
-    for (int t = warp; t < T; t += nwarps) {
-      const float e = eS[lane];
-      const float2 u = Uf[t];
-      const float2 v = lane < S ? V[t * S + lane] : u;
-      const float a = warp_sum_f(e * (v.x - u.x));
-      const float b = warp_sum_f(e * (v.y - u.y));
-      if (lane == 0) reinterpret_cast<float2*>(prow)[t] = make_float2(a, b);
+    for (int c = tid; c < 2 * T; c += nthreads) {
+      const int t = c >> 1;
+      const float* Vt = reinterpret_cast<const float*>(V + t * S) + (c & 1);
+      const float u = reinterpret_cast<const float*>(Uf + t)[c & 1];
+      float a = 0.0f;
+      for (int s = 0; s < S; ++s) a = fmaf(eS[s], Vt[2 * s] - u, a);
+      prow[c] = a;
     }
   }
 
   // ---- two-level last-arriver merge.  The CTA's writes are published by
   // one thread: barrier, fence, ticket; the last arriver fences again before
-  // the barrier that releases its threads to read the others' partials.
+  // the barrier that releases its threads to read the others' partials.  It
+  // takes (and clears) the group's minimum word, the exact minimum of its
+  // members' rho.
   __syncthreads();
   const int g = tile / D.GT;
   const int m0 = g * D.GT;
   const int members = min(D.GT, D.nTiles - m0);
+  unsigned* minw = D.counters + D.nGroups + 1;
   if (tid == 0) {
     __threadfence();
     unsigned tk = atomicAdd(&D.counters[g], 1u);
     ts.flag = (tk == (unsigned)(members - 1));
-    if (ts.flag) __threadfence();
+    if (ts.flag) {
+      __threadfence();
+      ts.ref = key_min(atomicExch(&minw[g], 0u));
+      D.counters[g] = 0u;
+    }
   }
   __syncthreads();
   if (!ts.flag) return;
   float* scl = reinterpret_cast<float*>(smem + L.scl);
   float* col_hi = reinterpret_cast<float*>(smem + L.colhi);
   float* col_lo = reinterpret_cast<float*>(smem + L.collo);
-  FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
   const int ncol = 2 * T;
-  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, D.inv_lambda_f, scl,
-                 &ts.rho, &ts.Z, col_hi, col_lo, mbuf, tid, nthreads);
+  FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
+  float2* zi = reinterpret_cast<float2*>(smem + L.region + merge_buf_bytes(ncol, nthreads));
+  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
+                 D.inv_lambda_f, scl, zi, mbuf, &ts.Z, col_hi, col_lo, tid, nthreads);
   if (D.nGroups > 1) {
     for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
     if (tid == 0) {
-      D.gpart_rz[g] = make_float4(ts.rho.hi, ts.rho.lo, ts.Z.hi, ts.Z.lo);
-      D.counters[g] = 0u;
+      D.gpart_rz[g] = make_float4(ts.ref, 0.0f, ts.Z.hi, ts.Z.lo);
+      atomicMax(&minw[D.nGroups], min_key(ts.ref));
     }
     __syncthreads();
     if (tid == 0) {
       __threadfence();
       unsigned tk = atomicAdd(&D.counters[D.nGroups], 1u);
       ts.flag = (tk == (unsigned)(D.nGroups - 1));
-      if (ts.flag) __threadfence();
+      if (ts.flag) {
+        __threadfence();
+        ts.ref = key_min(atomicExch(&minw[D.nGroups], 0u));
+        D.counters[D.nGroups] = 0u;
+      }
     }
     __syncthreads();
     if (!ts.flag) return;
-    merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, D.inv_lambda_f, scl, &ts.rho, &ts.Z,
-                   col_hi, col_lo, mbuf, tid, nthreads);
-    if (tid == 0) D.counters[D.nGroups] = 0u;
-  } else if (tid == 0) {
-    D.counters[0] = 0u;  // one group: its merge was the final one
+    merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
+                   &ts.Z, col_hi, col_lo, tid, nthreads);
   }
+  if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
   final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
 }
 

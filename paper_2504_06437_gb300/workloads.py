@@ -5,14 +5,14 @@ parameter sets and straight-line reference trajectories.  It holds none of
 the controller's arithmetic, and both the CUDA path and the CPU oracle are fed
 from it.  Every draw uses ``numpy.random.Generator(PCG64(seed))``.
 
-The paper publishes no obstacle layouts (Sec. IV gives only counts and radii),
+The paper publishes no obstacle layouts (Sec. V gives only counts and radii),
 so these fields stand in for its missions:
 
 * ``unicycle_small``: 10 x 10 m field, 10 obstacles, r ~ U(0.3, 0.8) m,
   K=256, T=30, dt=0.05 s (kinematic unicycle, one shape point).
 * ``quad2d``: 20 x 10 m corridor, 40 obstacles, r ~ U(0.2, 0.6) m, K=4096,
   T=50, dt=0.02 s, planar quadrotor with seven shape points on its 0.4 m frame
-  (Sec. IV-A constants: m = 0.5 kg, I = 0.005 kg m^2, g = 9.81, thrust limit
+  (Sec. V-A constants: m = 0.5 kg, I = 0.005 kg m^2, g = 9.81, thrust limit
   0.981 N).
 * ``unicycle_stress``: 50 x 50 m field, 200 obstacles, r ~ U(0.1, 1.0) m,
   K=65536, T=100.
@@ -33,7 +33,7 @@ import numpy as np
 UNICYCLE = 0
 QUAD2D = 1
 
-# Planar quadrotor constants printed in Sec. IV-A (frame 0.4 m, mass 0.5 kg,
+# Planar quadrotor constants printed in Sec. V-A (frame 0.4 m, mass 0.5 kg,
 # inertia 0.005 kg m^2, g = 9.81 m/s^2, thrust limit 0.981 N).
 QUAD_MASS = 0.5
 QUAD_INERTIA = 0.005
@@ -78,7 +78,7 @@ def obstacle_field(g: np.random.Generator, J: int, lo, hi, r_lo: float,
 def base_params(model: int, K: int, T: int, dt: float, seed: int) -> dict:
     """Parameter dict shared by the oracle and the CUDA binding.  Values the
     paper prints are used where it prints them (gamma = 2 for the control
-    cost and mu = 0.4, Sec. IV-A/B); the rest follow the presets above."""
+    cost and mu = 0.4, Sec. V-A/B); the rest follow the presets above."""
     p = dict(model=model, K=K, T=T, dt=dt, seed=seed,
              ln_mu=0.0, ln_sigma=0.3, mu_coarse=0.4, gamma_ctrl=2.0,
              gamma_bas=0.5, R_B=1.0, C_coll=1.0e4, h_eps=1.0e-3,
