@@ -439,14 +439,22 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     const uint32_t it_hi = (uint32_t)(st->iter >> 32);
     const float L00 = st->L00, L10 = st->L10, L11 = st->L11;
     const float lo0 = D.umin[0], hi0 = D.umax[0], lo1 = D.umin[1], hi1 = D.umax[1];
+    // item i = t S + s; (t, s) stepped by nthreads without a division
+    const int dt = nthreads / S, ds = nthreads - dt * S;
+    int t = tid / S, s = tid - t * S;
 #pragma unroll 2
     for (int i = tid; i < T * S; i += nthreads) {
-      const int t = i / S, s = i - t * S;
       const uint4 r = philox4x32_10(make_uint4((uint32_t)(k0 + s), (uint32_t)t, it_lo, it_hi),
                                     D.key0, D.key1);
       const float2 du = nln_draw(r, L00, L10, L11, D.ln_mu, D.ln_sigma);
       const float2 u = Uf[t];
       V[i] = make_float2(fminf(fmaxf(u.x + du.x, lo0), hi0), fminf(fmaxf(u.y + du.y, lo1), hi1));
+      t += dt;
+      s += ds;
+      if (s >= S) {
+        s -= S;
+        ++t;
+      }
     }
   }
   __syncthreads();
