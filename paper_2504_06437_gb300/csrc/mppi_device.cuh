@@ -358,7 +358,9 @@ struct TileScratch {
 
 // Fused barrier over nunits (step, sample) units; unit u has pose pose[u]
 // and P shape points shp[0..P).  Each thread takes NPOS / P whole units at a
-// time (NPOS >= P), keeps their world points in registers and streams every
+// time (NPOS >= P), units base + k nthreads + tid (k < NPOS / P) so that
+// neighbouring lanes read neighbouring poses, keeps their world points in
+// registers and streams every
 // obstacle: h = |p - c|^2 - r^2 evaluated as fma(dx, dx, fma(dy, dy, -r^2)),
 // terms 1 / max(h, h_eps) added two obstacles at a time as (h1 + h2) / (h1 h2)
 // with the approximate reciprocal.  A unit's points are
@@ -373,12 +375,12 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
                                               float2* uB, int ustride, int tid, int nthreads) {
   const int upt = NPOS / P;  // units per thread per round
   const int used = upt * P;
-  for (int ub = tid * upt; ub < nunits; ub += nthreads * upt) {
+  for (int ub = tid; ub < nunits; ub += nthreads * upt) {  // ub: this round's first unit
     float X[NPOS], Y[NPOS], acc[NPOS], mn[NPOS];
     int uu = 0, p = 0;
 #pragma unroll
     for (int i = 0; i < NPOS; ++i) {
-      const int u = ub + uu;
+      const int u = ub + uu * nthreads;
       const bool ok = (i < used) && (u < nunits);
       const float4 ps = pose[ok ? u : ub];
       const float2 sh = shp[ok ? p : 0];
@@ -430,7 +432,7 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
         ff_add(f, acc[i]);
         coll |= (mn[i] <= 0.0f);
         if (++p == P) {
-          const int u = ub + uu;
+          const int u = ub + uu * nthreads;
           if (u < nunits) uB[(size_t)u * ustride] = make_float2(coll ? -f.hi : f.hi, f.lo);
           f.hi = 0.0f;
           f.lo = 0.0f;
