@@ -158,13 +158,21 @@ def barrier(ws):
 
 
 def allmax(ws, v):
+    """Maximum of v over the ranks (the slowest rank's time)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(ws, units_per_rank, ms_max):
+    """Units per second of the whole job: every rank processes units_per_rank
+    units per step and the step lasts as long as the slowest rank (ms_max)."""
+    return ws * units_per_rank / (ms_max / 1e3)
 
 
 def world_for(workload, seed):
@@ -302,7 +310,7 @@ def run_batch(args, ws, rank, local):
     b.close()
     if rank != 0:
         return
-    line = {"metric": METRIC + " (batched)", "value": ws * work / (ms / 1e3), "unit": UNIT,
+    line = {"metric": METRIC + " (batched)", "value": whole_job_value(ws, work, ms), "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -317,7 +325,7 @@ def run_batch(args, ws, rank, local):
                              "form": "host loop: mppi_step + mppi_get_control per controller"},
             "batched_over_plain": plain_ms / ms,
             "batched_over_plain_synced": synced_ms / ms,
-            "e2e": {"value": ws * work / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+            "e2e": {"value": whole_job_value(ws, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(sum(8 * w.n * (w.params["T"] + 2) for w in worlds)),
                     "d2h_bytes_per_step": 16 * len(worlds),
                     "latency_ms": {"p50": 1e3 * float(np.percentile(wall, 50)),
@@ -530,7 +538,7 @@ def main():
     times_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     ms_local = float(times_ms.mean())
     ms = allmax(ws, ms_local)
-    value = ws * K * T / (ms / 1e3)
+    value = whole_job_value(ws, K * T, ms)
 
     # end to end through the host API (pinned staging inside the library)
     u0 = ctl.get_control()
@@ -567,7 +575,7 @@ def main():
                            tiling_source="autotuned" if tune_us else ("explicit" if args.tiling else "default")),
             "latency_ms": {"p50": float(np.percentile(times_ms, 50)),
                            "p99": float(np.percentile(times_ms, 99))},
-            "e2e": {"value": ws * K * T / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_value(ws, K * T, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                     "latency_ms": {"p50": 1e3 * float(np.percentile(e2e_t, 50)),
                                    "p99": 1e3 * float(np.percentile(e2e_t, 99))}},
