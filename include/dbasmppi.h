@@ -180,6 +180,16 @@ int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta,
 int mppi_debug_draws(const mppi_params* p, double S_e, uint64_t iter, int32_t K,
                      int32_t T, uint32_t* raw, float* du);
 
+/* Diagnostic of the bounded device wait that guards the obstacle staging
+ * (a bulk copy completing on an mbarrier): one CTA waits on a fresh
+ * mbarrier for at most max_cycles SM clock cycles (1 .. 4e9).  With
+ * arrive = 1 one thread arrives first, so the wait completes; with
+ * arrive = 0 nothing arrives and the bound runs out.  Returns MPPI_OK when
+ * the wait completed, MPPI_ETIMEOUT when the bound expired (the device stays
+ * usable), MPPI_EINVAL for a bound out of range, MPPI_ECUDA.  Synchronises.
+ * The paper has no counterpart; this is test support for the failure path. */
+int mppi_debug_wait_probe(int64_t max_cycles, int32_t arrive);
+
 /* One step without any device allocation and without a context, for callers
  * that may not allocate once they run: real-time control loops that keep
  * every step's latency bounded (cudaMalloc can block and synchronise the

@@ -122,6 +122,7 @@ def load():
     lib.mppi_destroy.argtypes = [vp]
     lib.mppi_debug_draws.argtypes = [C.POINTER(Params), C.c_double, C.c_uint64, C.c_int32,
                                      C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
+    lib.mppi_debug_wait_probe.argtypes = [C.c_int64, C.c_int32]
     lib.mppi_autotune.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.c_int32,
                                   C.POINTER(Tiling), C.POINTER(C.c_float)]
     lib.mppi_batch_create.argtypes = [C.c_int32, C.c_size_t, C.POINTER(vp)]

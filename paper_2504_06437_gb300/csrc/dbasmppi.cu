@@ -55,6 +55,16 @@ __global__ void weights_kernel(const double* __restrict__ costs, int K,
 }
 
 // Raw Philox words and NLN draws of the device generator for k < K, t < T.
+// One CTA waits on a fresh mbarrier (see mppi_debug_wait_probe).
+__global__ void wait_probe_kernel(long long max_cycles, int arrive, int* expired) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+  const bool ok = mbar_wait(&bar, 0u, 1 << 30, max_cycles);
+  if (threadIdx.x == 0) *expired = ok ? 0 : 1;
+}
+
 __global__ void draws_kernel(int K, int T, uint32_t k0, uint32_t k1, uint32_t it_lo, uint32_t it_hi,
                              float L00, float L10, float L11, float ln_mu, float ln_sigma,
                              uint32_t* __restrict__ raw, float* __restrict__ du) {
@@ -637,6 +647,21 @@ int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta, int32_
   prep_kernel<<<1, 256, 0, c->own>>>(c->D, 0);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->own));
+  return MPPI_OK;
+}
+
+extern "C" int mppi_debug_wait_probe(int64_t max_cycles, int32_t arrive) {
+  if (max_cycles < 1 || max_cycles > 4000000000ll)
+    return fail(MPPI_EINVAL, "max_cycles must be in [1, 4e9]");
+  int* d = nullptr;
+  CK(cudaMalloc((void**)&d, sizeof(int)));
+  wait_probe_kernel<<<1, 32>>>((long long)max_cycles, arrive ? 1 : 0, d);
+  int h = -1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(MPPI_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+  if (h != 0) return fail(MPPI_ETIMEOUT, "the bounded device wait expired (probe)");
   return MPPI_OK;
 }
 

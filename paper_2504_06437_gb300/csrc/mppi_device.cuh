@@ -321,9 +321,17 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Bounded wait on an mbarrier phase; false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls) {
+// One arrival on an mbarrier (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait on an mbarrier phase: at most max_polls tries and max_cycles
+// SM clock cycles (a try may suspend the thread for a while); false if a
+// bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls,
+                                          long long max_cycles) {
   uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
   for (int i = 0; i < max_polls; ++i) {
     uint32_t done;
     asm volatile(
@@ -333,6 +341,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if (clock64() - t0 > max_cycles) break;
   }
   return false;
 }

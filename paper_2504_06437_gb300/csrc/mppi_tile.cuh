@@ -7,6 +7,7 @@
 namespace dbm {
 
 constexpr int kTmaPolls = 1 << 22;
+constexpr long long kTmaWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 // Obstacle staging: 1 = bulk TMA copy into shared memory (mbarrier
 // completion), 0 = coalesced loads by all threads.
@@ -389,10 +390,10 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   }
   if (J > 0) {
 #if DBM_STAGE_TMA
-    bool ok = mbar_wait(&ts.mbar, mbar_phase, kTmaPolls);
+    bool ok = mbar_wait(&ts.mbar, mbar_phase, kTmaPolls, kTmaWaitCycles);
     if (!ok) {
       if (tid == 0) atomicExch(&st->status, kStatusTimeout);
-      mbar_wait(&ts.mbar, mbar_phase, kTmaPolls);
+      mbar_wait(&ts.mbar, mbar_phase, kTmaPolls, kTmaWaitCycles);
     }
     mbar_phase ^= 1u;  // every thread flips its own copy
     const double* raw = reinterpret_cast<const double*>(smem + L.region);

@@ -219,6 +219,19 @@ def test_stress_config_sampled(gpu, orc):
     assert np.all(dbg["Ustar"] <= np.array(p["u_max"]) + 1e-12)
 
 
+def test_bounded_device_wait_expires_and_device_stays_usable(gpu, orc):
+    """The wait that guards the obstacle staging is bounded: on a barrier that
+    nothing completes it gives up after its cycle limit (about 1 ms here) and
+    the host sees MPPI_ETIMEOUT; the device then runs a normal step that
+    matches the oracle.  No fault or hang is involved."""
+    lib = gpu.load()
+    assert lib.mppi_debug_wait_probe(2_000_000, 1) == gpu.MPPI_OK
+    assert lib.mppi_debug_wait_probe(2_000_000, 0) == gpu.MPPI_ETIMEOUT
+    assert b"expired" in lib.mppi_last_error()
+    assert lib.mppi_debug_wait_probe(0, 0) == gpu.MPPI_EINVAL
+    run_pair(gpu, orc, W.unicycle_small(3), steps=1)
+
+
 def test_checkpoint_resume_bit_exact(gpu, orc):
     w = W.quad2d(7, K=512, T=30)
     p = w.params
