@@ -240,7 +240,15 @@ def run_batch(args, ws, rank, local):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    policy, tune_ms = None, None
+    if not args.no_autotune:
+        policy, tune_ms = binding.batch_autotune([w.params for w in worlds],
+                                                 [w.obstacles for w in worlds], iters=3,
+                                                 pool_bytes=6 << 30)
     b = binding.Batch(len(worlds), 6 << 30)
+    if policy:
+        b.set_policy(policy)
+    used_policy = b.get_policy()
     slots = [b.add(w.params, w.obstacles) for w in worlds]
     x0s = [w.x_start for w in worlds]
     xrefs = [w.reference(w.x_start) for w in worlds]
@@ -317,7 +325,9 @@ def run_batch(args, ws, rank, local):
             "config": {"workload": f"batch_mix: {len(worlds)} controllers, half unicycle half planar "
                                    "quadrotor, K log-uniform 1024..16384, T 20..80, 5..300 obstacles",
                        "sample_steps_per_step": work, "l2": "flushed between timed steps (256 MB write)",
-                       "graph": "CUDA graph replay of copy-in, persistent kernel, copy-out"},
+                       "graph": "CUDA graph replay of copy-in, persistent kernel, copy-out",
+                       "tiling_policy": used_policy,
+                       "tiling_source": "autotuned (mppi_batch_autotune)" if policy else "default"},
             "latency_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
             "plain": {"value": work / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
                       "form": "one launch per controller, back to back on one stream"},

@@ -273,6 +273,35 @@ int mppi_batch_info(mppi_batch* b, int32_t slot, mppi_tiling* t, uint64_t* bytes
 /* Enable (default) or disable CUDA-graph capture and replay of the step. */
 int mppi_batch_set_graph(mppi_batch* b, int32_t enable);
 
+/* Tiling policy of a batch: the launch shape given to controllers that
+ * mppi_batch_add receives without an explicit tiling, per model (index
+ * MPPI_UNICYCLE, MPPI_QUAD2D).  samples_per_cta in 1..32 (capped at K);
+ * positions_per_thread 8 or 14, or 0 to choose from n_shape.  The batch
+ * kernel's CTAs have 256 threads.  Default: {32, 32}, {0, 0}. */
+typedef struct {
+  int32_t samples_per_cta[2];
+  int32_t positions_per_thread[2];
+} mppi_batch_policy;
+
+/* Set or read the policy used by later mppi_batch_add calls (controllers
+ * already added keep their shape).  Errors: MPPI_EINVAL (out of range). */
+int mppi_batch_set_policy(mppi_batch* b, const mppi_batch_policy* pol);
+int mppi_batch_get_policy(const mppi_batch* b, mppi_batch_policy* pol);
+
+/* Autotuner of the batched step.  For n representative controllers
+ * (parameters ps[i], obstacles cxcyrs[i] with Js[i] rows), each model's
+ * policy in turn is chosen from samples_per_cta {8, 16, 32} x
+ * positions_per_thread {8, 14} (the other model's held at its best so far):
+ * for each candidate a temporary batch of pool_bytes holds all n
+ * controllers, and `iters` graph-replayed steps of all of them (each from
+ * its x_goal) are timed with CUDA events after two untimed ones.  best
+ * receives the fastest policy and best_ms (may be NULL) its time per step.
+ * Candidates that do not fit the pool or the kernel are skipped.  Errors:
+ * MPPI_EINVAL, MPPI_ENOMEM (not even the default fits), MPPI_ECUDA. */
+int mppi_batch_autotune(const mppi_params* ps, const double* const* cxcyrs,
+                        const int32_t* Js, int32_t n, int32_t iters, size_t pool_bytes,
+                        mppi_batch_policy* best, float* best_ms);
+
 /* Release the batch and its pool.  NULL is a no-op. */
 int mppi_batch_destroy(mppi_batch* b);
 

@@ -95,6 +95,10 @@ class Tiling(C.Structure):
                 ("positions_per_thread", C.c_int32), ("chunk_steps", C.c_int32)]
 
 
+class BatchPolicy(C.Structure):
+    _fields_ = [("samples_per_cta", C.c_int32 * 2), ("positions_per_thread", C.c_int32 * 2)]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 
@@ -137,6 +141,11 @@ def load():
     lib.mppi_batch_info.argtypes = [vp, C.c_int32, C.POINTER(Tiling), C.POINTER(C.c_uint64),
                                     C.POINTER(C.c_uint64)]
     lib.mppi_batch_set_graph.argtypes = [vp, C.c_int32]
+    lib.mppi_batch_set_policy.argtypes = [vp, C.POINTER(BatchPolicy)]
+    lib.mppi_batch_get_policy.argtypes = [vp, C.POINTER(BatchPolicy)]
+    lib.mppi_batch_autotune.argtypes = [C.POINTER(Params), C.POINTER(_dp), C.POINTER(C.c_int32),
+                                        C.c_int32, C.c_int32, C.c_size_t,
+                                        C.POINTER(BatchPolicy), C.POINTER(C.c_float)]
     lib.mppi_batch_destroy.argtypes = [vp]
     lib.mppi_server_create.argtypes = [C.c_int32, C.c_size_t, C.c_int32, C.POINTER(vp)]
     lib.mppi_server_join.argtypes = [vp, C.POINTER(Params), _dp, _dp, C.c_int32,
@@ -408,6 +417,43 @@ class Batch:
 
     def set_graph(self, enable: bool):
         _check(load().mppi_batch_set_graph(self.h, int(bool(enable))))
+
+    def set_policy(self, policy: dict):
+        """Launch shape for later adds without an explicit tiling: dict with
+        per-model lists samples_per_cta and positions_per_thread."""
+        _check(load().mppi_batch_set_policy(self.h, C.byref(_policy(policy))))
+
+    def get_policy(self) -> dict:
+        pol = BatchPolicy()
+        _check(load().mppi_batch_get_policy(self.h, C.byref(pol)))
+        return _policy_dict(pol)
+
+
+def _policy(d: dict) -> BatchPolicy:
+    pol = BatchPolicy()
+    for m in range(2):
+        pol.samples_per_cta[m] = int(d["samples_per_cta"][m])
+        pol.positions_per_thread[m] = int(d["positions_per_thread"][m])
+    return pol
+
+
+def _policy_dict(pol: BatchPolicy) -> dict:
+    return dict(samples_per_cta=[pol.samples_per_cta[0], pol.samples_per_cta[1]],
+                positions_per_thread=[pol.positions_per_thread[0], pol.positions_per_thread[1]])
+
+
+def batch_autotune(cfgs, obstacles, iters: int = 3, pool_bytes: int = 2 << 30):
+    """Fastest batch policy for these controllers: (policy dict, ms per batched step)."""
+    n = len(cfgs)
+    ps = (Params * n)(*[make_params(c) for c in cfgs])
+    obs = [_f64(o).reshape(-1, 3) for o in obstacles]
+    ptrs = (_dp * n)(*[_ptr(o) if o.size else None for o in obs])
+    Js = (C.c_int32 * n)(*[o.shape[0] for o in obs])
+    pol = BatchPolicy()
+    ms = C.c_float()
+    _check(load().mppi_batch_autotune(ps, ptrs, Js, n, int(iters), int(pool_bytes), C.byref(pol),
+                                      C.byref(ms)))
+    return _policy_dict(pol), float(ms.value)
 
 
 class Server:

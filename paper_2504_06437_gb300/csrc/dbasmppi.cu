@@ -969,6 +969,7 @@ struct mppi_batch {
   cudaStream_t own = nullptr;
   int use_graph = 1;
   int max_smem = 0;
+  mppi_batch_policy pol = {{32, 32}, {0, 0}};
 };
 
 namespace {
@@ -1158,8 +1159,14 @@ int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
   if (tiling) {
     req = *tiling;
     req.threads = kBatchThreads;
+  } else {  // the batch's policy for this model
+    req.samples_per_cta = b->pol.samples_per_cta[p->model];
+    req.positions_per_thread = b->pol.positions_per_thread[p->model];
+    if (req.positions_per_thread > 0 && req.positions_per_thread < p->n_shape)
+      req.positions_per_thread = 0;
   }
-  if (req.samples_per_cta <= 0) req.samples_per_cta = p->K >= 32 ? 32 : p->K;
+  if (req.samples_per_cta <= 0) req.samples_per_cta = 32;
+  if (req.samples_per_cta > p->K) req.samples_per_cta = p->K;
   int smem = 0;
   rc = choose_tiling(p, &req, J, &s.tl, &smem);
   if (rc) return rc;
@@ -1460,6 +1467,27 @@ int mppi_batch_set_graph(mppi_batch* b, int32_t enable) {
   return MPPI_OK;
 }
 
+int mppi_batch_set_policy(mppi_batch* b, const mppi_batch_policy* pol) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (!pol) return fail(MPPI_EINVAL, "policy is NULL");
+  for (int m = 0; m < 2; ++m) {
+    if (pol->samples_per_cta[m] < 1 || pol->samples_per_cta[m] > 32)
+      return fail(MPPI_EINVAL, "samples_per_cta must be in 1..32");
+    const int np = pol->positions_per_thread[m];
+    if (np != 0 && np != 8 && np != 14)
+      return fail(MPPI_EINVAL, "positions_per_thread must be 0, 8 or 14");
+  }
+  b->pol = *pol;
+  return MPPI_OK;
+}
+
+int mppi_batch_get_policy(const mppi_batch* b, mppi_batch_policy* pol) {
+  if (!b) return fail(MPPI_ESTATE, "batch is NULL");
+  if (!pol) return fail(MPPI_EINVAL, "policy is NULL");
+  *pol = b->pol;
+  return MPPI_OK;
+}
+
 int mppi_batch_destroy(mppi_batch* b) {
   if (!b) return MPPI_OK;
   free_lane(b->lane);
@@ -1467,6 +1495,86 @@ int mppi_batch_destroy(mppi_batch* b) {
   cudaFree(b->d_descs);
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
+  return MPPI_OK;
+}
+
+// Time `iters` batched steps of n controllers added under policy pol to a
+// fresh batch of pool_bytes; false if a controller does not fit.
+static bool time_policy(const mppi_params* ps, const double* const* cxcyrs, const int32_t* Js,
+                        int32_t n, int32_t iters, size_t pool_bytes, const mppi_batch_policy& pol,
+                        const std::vector<double>& x0s, float* ms_out, int* rc_out) {
+  mppi_batch* b = nullptr;
+  *rc_out = mppi_batch_create(n, pool_bytes, &b);
+  if (*rc_out) return false;
+  bool ok = mppi_batch_set_policy(b, &pol) == MPPI_OK;
+  std::vector<int32_t> slots(n);
+  for (int i = 0; i < n && ok; ++i) {
+    const int rc = mppi_batch_add(b, &ps[i], nullptr, nullptr, cxcyrs ? cxcyrs[i] : nullptr,
+                                  Js ? Js[i] : 0, &slots[i]);
+    if (rc) {
+      *rc_out = rc;
+      ok = false;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ok) ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  for (int w = 0; w < 2 && ok; ++w)
+    ok = mppi_batch_step(b, slots.data(), n, x0s.data(), nullptr, nullptr) == MPPI_OK;
+  if (ok) ok = cudaStreamSynchronize(b->own) == cudaSuccess;
+  if (ok) {
+    cudaEventRecord(e0, b->own);
+    for (int i = 0; i < iters && ok; ++i)
+      ok = mppi_batch_step(b, slots.data(), n, x0s.data(), nullptr, nullptr) == MPPI_OK;
+    cudaEventRecord(e1, b->own);
+    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.0f;
+    if (ok) cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms / (float)iters;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  mppi_batch_destroy(b);
+  return ok;
+}
+
+int mppi_batch_autotune(const mppi_params* ps, const double* const* cxcyrs, const int32_t* Js,
+                        int32_t n, int32_t iters, size_t pool_bytes, mppi_batch_policy* best,
+                        float* best_ms) {
+  if (!ps || n < 1 || !best) return fail(MPPI_EINVAL, "bad controller list or output");
+  if (iters < 1) iters = 3;
+  std::vector<double> x0s((size_t)6 * n, 0.0);  // n x 6, each from its goal state
+  for (int i = 0; i < n; ++i) {
+    if (int rc = validate(&ps[i])) return rc;
+    for (int d = 0; d < 6; ++d) x0s[(size_t)i * 6 + d] = ps[i].x_goal[d];
+  }
+  mppi_batch_policy cur = {{32, 32}, {0, 0}};
+  float cur_ms = 0.0f;
+  int rc = 0;
+  if (!time_policy(ps, cxcyrs, Js, n, iters, pool_bytes, cur, x0s, &cur_ms, &rc))
+    return rc ? rc : fail(MPPI_ECUDA, "timing the default policy failed");
+  const int S_opts[3] = {8, 16, 32};
+  const int NP_opts[2] = {8, 14};
+  for (int m = 0; m < 2; ++m) {
+    bool present = false;
+    for (int i = 0; i < n; ++i) present = present || ps[i].model == m;
+    if (!present) continue;
+    for (int S : S_opts)
+      for (int NP : NP_opts) {
+        mppi_batch_policy cand = cur;
+        cand.samples_per_cta[m] = S;
+        cand.positions_per_thread[m] = NP;
+        if (S == cur.samples_per_cta[m] && NP == cur.positions_per_thread[m]) continue;
+        float ms = 0.0f;
+        int crc = 0;
+        if (time_policy(ps, cxcyrs, Js, n, iters, pool_bytes, cand, x0s, &ms, &crc) && ms < cur_ms) {
+          cur = cand;
+          cur_ms = ms;
+        }
+        cudaGetLastError();
+      }
+  }
+  *best = cur;
+  if (best_ms) *best_ms = cur_ms;
   return MPPI_OK;
 }
 

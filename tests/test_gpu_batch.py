@@ -127,3 +127,40 @@ def test_batch_matches_oracle(gpu, orc):
                 assert rel.max() <= 1e-4
                 np.testing.assert_allclose(u[i], ro["u0"], rtol=0, atol=1e-5)
                 np.testing.assert_allclose(st["U"], ro["U_next"], rtol=0, atol=1e-5)
+
+
+def test_batch_autotuned_policy_shapes_and_equals_alone(gpu):
+    """mppi_batch_autotune picks a per-model policy from timed batched steps;
+    a batch under that policy gives each new controller the policy's shape
+    (samples per CTA capped at K), and its results still equal the
+    one-controller launch of the same shape bit for bit."""
+    worlds = mix(4)
+    pol, ms = gpu.batch_autotune([w.params for w in worlds], [w.obstacles for w in worlds],
+                                 iters=2, pool_bytes=256 << 20)
+    assert ms > 0.0
+    for m in range(2):
+        assert pol["samples_per_cta"][m] in (8, 16, 32)
+        assert pol["positions_per_thread"][m] in (0, 8, 14)
+    with gpu.Batch(8, 256 << 20) as b:
+        with pytest.raises(gpu.MppiError):
+            b.set_policy(dict(samples_per_cta=[0, 32], positions_per_thread=[0, 0]))
+        with pytest.raises(gpu.MppiError):
+            b.set_policy(dict(samples_per_cta=[32, 32], positions_per_thread=[9, 0]))
+        b.set_policy(pol)
+        assert b.get_policy() == pol
+        slots = [b.add(w.params, w.obstacles) for w in worlds]
+        for w, s in zip(worlds, slots):
+            sh = b.slot_info(s)
+            m = int(w.params["model"])
+            assert sh["samples_per_cta"] == min(pol["samples_per_cta"][m], int(w.params["K"]))
+            if pol["positions_per_thread"][m]:
+                assert sh["positions_per_thread"] == pol["positions_per_thread"][m]
+        b.step(slots, [w.x_start for w in worlds], [w.reference(w.x_start) for w in worlds])
+        u_b = b.controls()
+        for i, (w, s) in enumerate(zip(worlds, slots)):
+            sh = b.slot_info(s)
+            with gpu.Controller(w.params, tiling=dict(samples_per_cta=sh["samples_per_cta"], threads=256,
+                                                      positions_per_thread=sh["positions_per_thread"])) as g:
+                g.set_obstacles(w.obstacles)
+                g.step(w.x_start, w.reference(w.x_start))
+                np.testing.assert_array_equal(u_b[i], g.get_control())
