@@ -113,7 +113,7 @@ __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a *
 
 // Tile merge geometry (merge_partials): row groups over the CTA's threads
 // and the bytes of their float-pair column sums.
-constexpr int kMergeLoads = 16;   // float2 loads in flight per thread
+constexpr int kMergeLoads = 16;   // float2 loads in flight per thread (two batches)
 constexpr int kMergeGroups = 32;  // row groups at most
 __host__ __device__ inline int merge_row_groups(int ncol, int nthreads) {
   const int ncp = ncol / 2;
@@ -507,16 +507,34 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
   const int ncell = RG * ncp;
   const int ldb = ncol + 1;  // buf row: the columns, then Z
   const float2* cols2 = reinterpret_cast<const float2*>(cols);
-  float2 v[kMergeLoads];
-  auto load = [&](int cell, int r0) {
+  // two batches of KB rows: the next batch is in flight while one is added
+  constexpr int KB = kMergeLoads / 2;
+  float2 va[KB], vb[KB];
+  auto load = [&](float2 (&v)[KB], int cell, int r0) {
     const int rg = cell / ncp, cp = cell - rg * ncp;
 #pragma unroll
-    for (int q = 0; q < kMergeLoads; ++q) {
+    for (int q = 0; q < KB; ++q) {
       const int i = rg + (r0 + q) * RG;
       v[q] = (cell < ncell && i < n) ? __ldcg(cols2 + (size_t)i * ncp + cp) : make_float2(0.0f, 0.0f);
     }
   };
-  load(tid, 0);
+  auto add = [&](const float2 (&v)[KB], int rg, int cp, int r0, FF& a0, FF& a1, FF& z) {
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int i = rg + (r0 + q) * RG;
+      if (i < n) {
+        const float sc = scl[i];
+        ff_add(a0, v[q].x * sc);
+        ff_add(a1, v[q].y * sc);
+        if (cp == 0) {
+          const float2 zz = zi[i];
+          ff_add_prod(z, sc, zz.x, zz.y);
+        }
+      }
+    }
+  };
+  load(va, tid, 0);  // issued before the scales are known
+  load(vb, tid, KB);
   for (int i = tid; i < n; i += nthreads) {
     const float4 c = __ldcg(rz + i);
     scl[i] = expf(-((c.x - ref) + c.y) * inv_lambda);
@@ -526,27 +544,21 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
   for (int cell = tid; cell < ncell; cell += nthreads) {
     const int rg = cell / ncp, cp = cell - rg * ncp;
     FF a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, z = {0.0f, 0.0f};
-    for (int r0 = 0;; r0 += kMergeLoads) {
-#pragma unroll
-      for (int q = 0; q < kMergeLoads; ++q) {
-        const int i = rg + (r0 + q) * RG;
-        if (i < n) {
-          const float sc = scl[i];
-          ff_add(a0, v[q].x * sc);
-          ff_add(a1, v[q].y * sc);
-          if (cp == 0) {
-            const float2 zz = zi[i];
-            ff_add_prod(z, sc, zz.x, zz.y);
-          }
-        }
-      }
-      if (rg + (r0 + kMergeLoads) * RG >= n) break;
-      load(cell, r0 + kMergeLoads);
+    for (int r0 = 0;; r0 += 2 * KB) {
+      add(va, rg, cp, r0, a0, a1, z);
+      if (rg + (r0 + KB) * RG >= n) break;
+      if (rg + (r0 + 2 * KB) * RG < n) load(va, cell, r0 + 2 * KB);
+      add(vb, rg, cp, r0 + KB, a0, a1, z);
+      if (rg + (r0 + 2 * KB) * RG >= n) break;
+      if (rg + (r0 + 3 * KB) * RG < n) load(vb, cell, r0 + 3 * KB);
     }
     buf[rg * ldb + 2 * cp] = a0;
     buf[rg * ldb + 2 * cp + 1] = a1;
     if (cp == 0) buf[rg * ldb + ncol] = z;
-    if (cell + nthreads < ncell) load(cell + nthreads, 0);
+    if (cell + nthreads < ncell) {
+      load(va, cell + nthreads, 0);
+      load(vb, cell + nthreads, KB);
+    }
   }
   __syncthreads();
   for (int c = tid; c <= ncol; c += nthreads) {
