@@ -95,9 +95,9 @@ typedef struct mppi_params {
 typedef struct mppi_tiling {
   int32_t samples_per_cta;  /* S, 1..32 */
   int32_t threads;          /* 64, 128, 256 or 512 */
-  int32_t positions_per_thread; /* 8, 14 or 16 world points per barrier
+  int32_t positions_per_thread; /* 8 or 14 world points per barrier
                                    thread, >= n_shape (whole units) */
-  int32_t chunk_steps;      /* time steps per chunk */
+  int32_t chunk_steps;      /* reserved: ignored on input, 0 on output */
 } mppi_tiling;
 
 typedef struct mppi_ctx mppi_ctx;
