@@ -15,9 +15,16 @@
 //              (step, sample) unit, its P shape points and every obstacle
 //              (Eq. 5, 13/15): each thread keeps whole units (NPOS world
 //              points) in registers, streams the obstacle set from shared
-//              memory (broadcast reads) and sums each unit's points exactly
-//              into a float pair, written over the unit's pose;
-//   costs      one warp per sample adds the barrier-state and collision costs.
+//              memory (broadcast reads), adds two obstacles per approximate
+//              reciprocal, and sums each unit's points exactly into a float
+//              pair, written over the unit's pose;
+//   costs      one warp per sample adds the barrier-state and collision costs;
+//   partials   the tile's minimum cost, its exponentiated weights, their sum Z
+//              and the 2T weighted column sums of the perturbations (Eq. 4);
+//   merge      the last tile to finish (a ticket per group of tiles) merges
+//              the partials log-sum-exp style against the exact minimum over
+//              the tiles, then runs the final stage (U*, nominal rollout, S_e,
+//              shift).
 // The DBaS recursion of Eq. 7, w_t = b_t + gamma (w_{t-1} - beta_d), is
 // linear, so its cost sum is evaluated in unrolled form:
 //   sum_{t=1..T} w_t = sum_s c_s b_s + beta_0 g1 - gamma beta_d csum,
@@ -28,11 +35,11 @@
 //
 // Precision: the rollout runs in FP32 in a frame whose origin is the
 // measured position (obstacles and reference are moved into it in FP64 then
-// rounded), so coordinates stay small; the per-sample cost is accumulated as
-// an unevaluated float pair (TwoSum / TwoProd), the parts of the cost common
-// to all samples are added in FP64, the normaliser and the tile minima are
-// FP64, and the cross-tile sums of weighted perturbations are compensated
-// FP32.
+// rounded), so coordinates stay small; the per-sample cost is an unevaluated
+// float pair (TwoSum / TwoProd) relative to a base, the part of the cost
+// common to all samples, formed in FP64; the minima, the normaliser Z and the
+// weighted sums of perturbations are float pairs, merged across tiles with
+// float-pair arithmetic; U* is formed in FP64 from them.
 #pragma once
 
 #include <cuda_runtime.h>
