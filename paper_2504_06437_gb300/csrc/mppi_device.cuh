@@ -120,7 +120,7 @@ __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a *
 
 // Tile merge geometry (merge_partials): row groups over the CTA's threads
 // and the bytes of their float-pair column sums.
-constexpr int kMergeLoads = 16;   // float2 loads in flight per thread (two batches)
+constexpr int kMergeLoads = 16;   // float2 loads in flight per thread
 constexpr int kMergeGroups = 32;  // row groups at most
 __host__ __device__ inline int merge_row_groups(int ncol, int nthreads) {
   const int ncp = ncol / 2;
@@ -503,8 +503,15 @@ __device__ __forceinline__ float key_min(unsigned k) {
 // (tid / ncp, tid % ncp), i.e. rows rg, rg + RG, ... of that pair, up to
 // kMergeLoads rows in flight; the threads with cp = 0 also add s_i Z_i.  The
 // row groups are then added in order.  All threads of the CTA call it.
+// PIPELINED: the rows in flight are two batches of kMergeLoads / 2, the next
+// loading while one is added; otherwise one batch of kMergeLoads, added
+// before the next is loaded.  Both add the rows in the same order (the same
+// bits).  The two-batch form is faster in the one-controller step kernels
+// (a 256-sample step: 24.2 against 26.4 us); the one-batch form in the
+// persistent batch kernel (64 mixed controllers: 3.31 against 4.04 ms).
 // Shared memory: scl (n floats), zi (n float2), buf (merge_buf_bytes).
 // Outputs in shared memory: *Z_out, col_hi/col_lo[ncol].
+template <bool PIPELINED>
 __device__ inline void merge_partials(int n, const float4* rz, const float* cols, int ncol,
                                       float ref, float inv_lambda, float* scl, float2* zi, FF* buf,
                                       FF* Z_out, float* col_hi, float* col_lo, int tid,
@@ -514,9 +521,8 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
   const int ncell = RG * ncp;
   const int ldb = ncol + 1;  // buf row: the columns, then Z
   const float2* cols2 = reinterpret_cast<const float2*>(cols);
-  // two batches of KB rows: the next batch is in flight while one is added
-  constexpr int KB = kMergeLoads / 2;
-  float2 va[KB], vb[KB];
+  constexpr int KB = PIPELINED ? kMergeLoads / 2 : kMergeLoads;
+  float2 va[KB], vb[KB];  // vb: the second batch (PIPELINED only)
   auto load = [&](float2 (&v)[KB], int cell, int r0) {
     const int rg = cell / ncp, cp = cell - rg * ncp;
 #pragma unroll
@@ -541,7 +547,7 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
     }
   };
   load(va, tid, 0);  // issued before the scales are known
-  load(vb, tid, KB);
+  if constexpr (PIPELINED) load(vb, tid, KB);
   for (int i = tid; i < n; i += nthreads) {
     const float4 c = __ldcg(rz + i);
     scl[i] = expf(-((c.x - ref) + c.y) * inv_lambda);
@@ -551,20 +557,28 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
   for (int cell = tid; cell < ncell; cell += nthreads) {
     const int rg = cell / ncp, cp = cell - rg * ncp;
     FF a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, z = {0.0f, 0.0f};
-    for (int r0 = 0;; r0 += 2 * KB) {
-      add(va, rg, cp, r0, a0, a1, z);
-      if (rg + (r0 + KB) * RG >= n) break;
-      if (rg + (r0 + 2 * KB) * RG < n) load(va, cell, r0 + 2 * KB);
-      add(vb, rg, cp, r0 + KB, a0, a1, z);
-      if (rg + (r0 + 2 * KB) * RG >= n) break;
-      if (rg + (r0 + 3 * KB) * RG < n) load(vb, cell, r0 + 3 * KB);
+    if constexpr (PIPELINED) {
+      for (int r0 = 0;; r0 += 2 * KB) {
+        add(va, rg, cp, r0, a0, a1, z);
+        if (rg + (r0 + KB) * RG >= n) break;
+        if (rg + (r0 + 2 * KB) * RG < n) load(va, cell, r0 + 2 * KB);
+        add(vb, rg, cp, r0 + KB, a0, a1, z);
+        if (rg + (r0 + 2 * KB) * RG >= n) break;
+        if (rg + (r0 + 3 * KB) * RG < n) load(vb, cell, r0 + 3 * KB);
+      }
+    } else {
+      for (int r0 = 0;; r0 += KB) {
+        add(va, rg, cp, r0, a0, a1, z);
+        if (rg + (r0 + KB) * RG >= n) break;
+        load(va, cell, r0 + KB);
+      }
     }
     buf[rg * ldb + 2 * cp] = a0;
     buf[rg * ldb + 2 * cp + 1] = a1;
     if (cp == 0) buf[rg * ldb + ncol] = z;
     if (cell + nthreads < ncell) {
       load(va, cell + nthreads, 0);
-      load(vb, cell + nthreads, KB);
+      if constexpr (PIPELINED) load(vb, cell + nthreads, KB);
     }
   }
   __syncthreads();

@@ -331,7 +331,8 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 
 // One tile of one controller.  ts.mbar must be initialised; mbar_phase is
 // each thread's own copy of the parity of the barrier's next completion.
-template <int MODEL, int NPOS>
+// PIPELINED_MERGE selects the form of merge_partials (the same result).
+template <int MODEL, int NPOS, bool PIPELINED_MERGE>
 __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
                          const double* __restrict__ xrefg, char* smem, TileScratch& ts,
                          uint32_t& mbar_phase, double* u0_out = nullptr) {
@@ -360,33 +361,57 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
 
   // ---- prologue: stage obstacles (TMA bulk copy), per-step constants
   __syncthreads();  // previous use of shared memory by this CTA is over
-  if (tid == 0) {  // read early: only the final stage uses them
-    ts.S_e_used = st->S_e;
-    ts.iter = st->iter;
-  }
 #if DBM_STAGE_TMA
   if (tid == 0 && J > 0)
     tma_bulk_g2s(smem + L.region, D.obst, (uint32_t)align_up(24 * J, 16), &ts.mbar);
 #endif
   if (tid < P) shp[tid] = make_float2(D.shape[2 * tid], D.shape[2 * tid + 1]);
+  // Loads ahead of stores: the shared-memory stores below go through
+  // pointers that the compiler cannot tell apart from the global arrays read
+  // here, so a load written after a store is issued only once that store's
+  // data has arrived, and interleaved loads and stores pay one memory round
+  // trip each.  Written in this order, the state words and the sequence's
+  // constants take one round trip and the reference rows (kXrefBatch per
+  // thread at a time) one more.  Issuing the reference loads before the
+  // constants' stores as well saves that second trip but costs registers
+  // that the 14-point barrier loop needs: slower at 14 points per thread.
   const double ox = x0g[0], oy = x0g[1];
-  if (tid < n) xi[tid] = tid < 2 ? 0.0f : (float)x0g[tid];
+  const double x0t = tid < n ? x0g[tid] : 0.0;
   double* Us = reinterpret_cast<double*>(smem + L.Us);
-  const float inv_Se = 1.0f / (float)st->S_e;  // a_t = a'_t / S_e
+  const double S_e = st->S_e;
+  const unsigned long long iter = tid == 0 ? st->iter : 0ull;
+  const float inv_Se = 1.0f / (float)S_e;  // a_t = a'_t / S_e
   for (int t = tid; t < T; t += nthreads) {
-    Uf[t] = D.cU[t];
-    const float2 a = D.cA[t];
+    const float2 u = D.cU[t], a = D.cA[t];
+    const float w = D.cw[t];
+    const double v0 = D.U[2 * t], v1 = D.U[2 * t + 1];
+    Uf[t] = u;
     Af[t] = make_float2(a.x * inv_Se, a.y * inv_Se);
-    cw[t] = D.cw[t];
-    Us[2 * t] = D.U[2 * t];  // for the final stage, should this CTA run it
-    Us[2 * t + 1] = D.U[2 * t + 1];
+    cw[t] = w;
+    Us[2 * t] = v0;  // for the final stage, should this CTA run it
+    Us[2 * t + 1] = v1;
   }
-  for (int i = tid; i < (T + 1) * n; i += nthreads) {
-    int d = i % n;
-    double v = xrefg[i];
-    if (d == 0) v -= ox;
-    if (d == 1) v -= oy;
-    xrf[i] = (float)v;
+  {
+    constexpr int kXrefBatch = 4;
+    const int NX = (T + 1) * n;
+    for (int i0 = tid; i0 < NX; i0 += kXrefBatch * nthreads) {
+      double v[kXrefBatch];
+#pragma unroll
+      for (int r = 0; r < kXrefBatch; ++r) {
+        const int i = i0 + r * nthreads;
+        v[r] = i < NX ? xrefg[i] : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < kXrefBatch; ++r) {
+        const int i = i0 + r * nthreads, d = i % n;
+        if (i < NX) xrf[i] = (float)(d == 0 ? v[r] - ox : d == 1 ? v[r] - oy : v[r]);
+      }
+    }
+  }
+  if (tid < n) xi[tid] = tid < 2 ? 0.0f : (float)x0t;
+  if (tid == 0) {  // read early: only the final stage uses them
+    ts.S_e_used = S_e;
+    ts.iter = iter;
   }
   if (J > 0) {
 #if DBM_STAGE_TMA
@@ -578,7 +603,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   const int ncol = 2 * T;
   FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
   float2* zi = reinterpret_cast<float2*>(smem + L.region + merge_buf_bytes(ncol, nthreads));
-  merge_partials(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
+  merge_partials<PIPELINED_MERGE>(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
                  D.inv_lambda_f, scl, zi, mbuf, &ts.Z, col_hi, col_lo, tid, nthreads);
   if (D.nGroups > 1) {
     for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
@@ -599,7 +624,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     }
     __syncthreads();
     if (!ts.flag) return;
-    merge_partials(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
+    merge_partials<PIPELINED_MERGE>(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
                    &ts.Z, col_hi, col_lo, tid, nthreads);
   }
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
