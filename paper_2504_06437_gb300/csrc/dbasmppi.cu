@@ -840,9 +840,10 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
 
 // ------------------------------------------------------------------------
 // Autotuner: time the candidate launch shapes on the problem itself and keep
-// the fastest.  Candidates: samples per CTA in {2, 4, 7, 10, 14, 20, 27, 32}
-// (those giving at most 16 CTAs per SM), threads in {128, 256, 512}, world
-// points per barrier thread in {8, 14, 16} (whole units).  Each candidate runs
+// the fastest.  Candidates: samples per CTA in {2, 4, 5, 7, 8, 10, 11, 12, 13,
+// 14, 16, 20, 24, 27, 32} (those giving at most 16 CTAs per SM; neighbouring
+// values change how the last wave of CTAs fills the SMs), threads in
+// {128, 256, 512}, world points per barrier thread in {8, 14} (whole units).  Each candidate runs
 // `iters` steps after two warm-up steps on a scratch controller, timed with
 // CUDA events; the controller state is reset so every candidate sees the same
 // inputs.
@@ -853,7 +854,7 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
   if (!best) return fail(MPPI_EINVAL, "best is NULL");
   if (iters < 1) iters = 5;
   const int sms = num_sms();
-  const int S_opts[8] = {2, 4, 7, 10, 14, 20, 27, 32};
+  const int S_opts[] = {2, 4, 5, 7, 8, 10, 11, 12, 13, 14, 16, 20, 24, 27, 32};
   const int NT_opts[3] = {128, 256, 512};
   const int NP_opts[2] = {8, 14};
   const int n = state_dim(p->model);

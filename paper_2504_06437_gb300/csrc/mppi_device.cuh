@@ -246,6 +246,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// min(a, b, c) in one instruction (three-input PTX min, sm_100 and later);
+// exact, as min(min(a, b), c).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float y;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+  return y;
+}
+
 // Unevaluated float pair accumulated with Knuth's TwoSum.
 struct FF {
   float hi, lo;
@@ -379,20 +387,27 @@ struct TileScratch {
 // registers and streams every
 // obstacle: h = |p - c|^2 - r^2 evaluated as fma(dx, dx, fma(dy, dy, -r^2)),
 // terms 1 / max(h, h_eps) added two obstacles at a time as (h1 + h2) / (h1 h2)
-// with the approximate reciprocal.  A unit's points are
-// summed exactly (TwoSum) into (hi, lo), stored at uB[u * ustride]; the sign
-// bit of hi marks a unit in which some h <= 0 (collision).  A thread reads
-// the poses of its units before it writes their sums, so uB may overlay
-// pose.
+// with the approximate reciprocal.  The points are held in packed pairs and
+// the subtractions, fmas, sums and products are packed two-lane FP32
+// instructions (each lane the same round-to-nearest operation as the scalar
+// one, so the results are the scalar loop's bit for bit): one issue slot
+// for two points, where the loop is bound by instruction issue.  A unit's
+// points are summed exactly (TwoSum) into (hi, lo), stored at
+// uB[u * ustride]; the sign bit of hi marks a unit in which some h <= 0
+// (collision).  A thread reads the poses of its units before it writes their
+// sums, so uB may overlay pose.
 template <int NPOS>
 __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const float4* pose,
                                               const float2* __restrict__ shp,
                                               const float4* __restrict__ obs4, float h_eps,
                                               float2* uB, int ustride, int tid, int nthreads) {
+  static_assert(NPOS % 2 == 0, "points are held in packed pairs");
+  constexpr int NP2 = NPOS / 2;
   const int upt = NPOS / P;  // units per thread per round
   const int used = upt * P;
   for (int ub = tid; ub < nunits; ub += nthreads * upt) {  // ub: this round's first unit
-    float X[NPOS], Y[NPOS], acc[NPOS], mn[NPOS];
+    float2 X2[NP2], Y2[NP2], acc2[NP2];  // points 2k and 2k + 1
+    float mn[NPOS];
     int uu = 0, p = 0;
 #pragma unroll
     for (int i = 0; i < NPOS; ++i) {
@@ -400,15 +415,23 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
       const bool ok = (i < used) && (u < nunits);
       const float4 ps = pose[ok ? u : ub];
       const float2 sh = shp[ok ? p : 0];
-      X[i] = fmaf(ps.z, sh.x, fmaf(-ps.w, sh.y, ps.x));
-      Y[i] = fmaf(ps.w, sh.x, fmaf(ps.z, sh.y, ps.y));
-      acc[i] = 0.0f;
+      const float X = fmaf(ps.z, sh.x, fmaf(-ps.w, sh.y, ps.x));
+      const float Y = fmaf(ps.w, sh.x, fmaf(ps.z, sh.y, ps.y));
+      if (i & 1) {
+        X2[i >> 1].y = X;
+        Y2[i >> 1].y = Y;
+      } else {
+        X2[i >> 1].x = X;
+        Y2[i >> 1].x = Y;
+      }
       mn[i] = __int_as_float(0x7f800000);
       if (++p == P) {
         p = 0;
         ++uu;
       }
     }
+#pragma unroll
+    for (int k = 0; k < NP2; ++k) acc2[k] = make_float2(0.0f, 0.0f);
     // obstacles in pairs: 1/h1 + 1/h2 = (h1 + h2) / (h1 h2), one reciprocal
     // for two terms (h1 h2 stays finite for |p - c| < 4e9 m and h_eps >= 1e-18);
     // with more points per thread the pair's temporaries would not fit
@@ -416,26 +439,37 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
     if constexpr (NPOS <= 8)
     for (; j + 1 < J; j += 2) {
       const float4 o = obs4[j], q = obs4[j + 1];
+      const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y);
+      const float2 noz = make_float2(o.z, o.z);
+      const float2 nqx = make_float2(-q.x, -q.x), nqy = make_float2(-q.y, -q.y);
+      const float2 nqz = make_float2(q.z, q.z);
 #pragma unroll
-      for (int i = 0; i < NPOS; ++i) {
-        const float dx = X[i] - o.x, dy = Y[i] - o.y;
-        const float ex = X[i] - q.x, ey = Y[i] - q.y;
-        float h1 = fmaf(dx, dx, fmaf(dy, dy, o.z));
-        float h2 = fmaf(ex, ex, fmaf(ey, ey, q.z));
-        mn[i] = fminf(mn[i], fminf(h1, h2));
-        h1 = fmaxf(h1, h_eps);
-        h2 = fmaxf(h2, h_eps);
-        acc[i] = fmaf(h1 + h2, rcp_approx(h1 * h2), acc[i]);
+      for (int k = 0; k < NP2; ++k) {
+        const float2 dx = __fadd2_rn(X2[k], nox), dy = __fadd2_rn(Y2[k], noy);
+        const float2 ex = __fadd2_rn(X2[k], nqx), ey = __fadd2_rn(Y2[k], nqy);
+        float2 h1 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, noz));
+        float2 h2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, nqz));
+        mn[2 * k] = fmin3(mn[2 * k], h1.x, h2.x);
+        mn[2 * k + 1] = fmin3(mn[2 * k + 1], h1.y, h2.y);
+        h1 = make_float2(fmaxf(h1.x, h_eps), fmaxf(h1.y, h_eps));
+        h2 = make_float2(fmaxf(h2.x, h_eps), fmaxf(h2.y, h_eps));
+        const float2 pr = __fmul2_rn(h1, h2);
+        const float2 r = make_float2(rcp_approx(pr.x), rcp_approx(pr.y));
+        acc2[k] = __ffma2_rn(__fadd2_rn(h1, h2), r, acc2[k]);
       }
     }
     for (; j < J; ++j) {
       const float4 o = obs4[j];
+      const float2 nox = make_float2(-o.x, -o.x), noy = make_float2(-o.y, -o.y);
+      const float2 noz = make_float2(o.z, o.z);
 #pragma unroll
-      for (int i = 0; i < NPOS; ++i) {
-        const float dx = X[i] - o.x, dy = Y[i] - o.y;
-        const float h = fmaf(dx, dx, fmaf(dy, dy, o.z));
-        mn[i] = fminf(mn[i], h);
-        acc[i] += rcp_approx(fmaxf(h, h_eps));
+      for (int k = 0; k < NP2; ++k) {
+        const float2 dx = __fadd2_rn(X2[k], nox), dy = __fadd2_rn(Y2[k], noy);
+        const float2 h = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, noz));
+        mn[2 * k] = fminf(mn[2 * k], h.x);
+        mn[2 * k + 1] = fminf(mn[2 * k + 1], h.y);
+        acc2[k] = __fadd2_rn(acc2[k], make_float2(rcp_approx(fmaxf(h.x, h_eps)),
+                                                  rcp_approx(fmaxf(h.y, h_eps))));
       }
     }
     FF f = {0.0f, 0.0f};
@@ -445,7 +479,7 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
 #pragma unroll
     for (int i = 0; i < NPOS; ++i) {
       if (i < used) {
-        ff_add(f, acc[i]);
+        ff_add(f, (i & 1) ? acc2[i >> 1].y : acc2[i >> 1].x);
         coll |= (mn[i] <= 0.0f);
         if (++p == P) {
           const int u = ub + uu * nthreads;
