@@ -318,6 +318,21 @@ def run_batch(args, ws, rank, local):
     b.close()
     if rank != 0:
         return
+    # the same FP32 issue roofline as the one-controller step, over the sum
+    # of the controllers' algorithmic work (the batch kernel is the only
+    # kernel in the timed region)
+    ops = sum(algorithmic_ops(int(w.params["K"]), int(w.params["T"]),
+                              int(np.asarray(w.params["shape"]).reshape(-1, 2).shape[0]),
+                              int(w.obstacles.shape[0])) for w in worlds)
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_tops = sms * 128 * f_max / 1e12
+    achieved_tops = ops / (ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TOP/s",
+                "frac": achieved_tops / peak_tops, "traffic": None, "kernel": "batch_kernel",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz",
+                "ops_per_launch": ops}
     line = {"metric": METRIC + " (batched)", "value": whole_job_value(ws, work, ms), "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -340,6 +355,7 @@ def run_batch(args, ws, rank, local):
                     "d2h_bytes_per_step": 16 * len(worlds),
                     "latency_ms": {"p50": 1e3 * float(np.percentile(wall, 50)),
                                    "p99": 1e3 * float(np.percentile(wall, 99))}},
+            "roofline": roofline,
             "gpu_launches": args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
