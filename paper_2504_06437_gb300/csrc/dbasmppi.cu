@@ -78,9 +78,10 @@ __global__ void draws_kernel(int K, int T, uint32_t k0, uint32_t k1, uint32_t it
 
 using StepFn = void (*)(CtrlDesc, const double*, const double*);
 
-StepFn pick_kernel(int model, int npos) {
-  if (model == MPPI_UNICYCLE) return npos == 14 ? step_u14 : step_u8;
-  return npos == 14 ? step_q14 : step_q8;
+StepFn pick_kernel(int model, int npos, bool r80) {
+  if (model == MPPI_UNICYCLE)
+    return npos == 14 ? (r80 ? step_u14_r80 : step_u14) : (r80 ? step_u8_r80 : step_u8);
+  return npos == 14 ? (r80 ? step_q14_r80 : step_q14) : (r80 ? step_q8_r80 : step_q8);
 }
 
 // World points a barrier thread holds: whole units of P points each; the
@@ -183,6 +184,49 @@ int max_smem_optin() {
   if (cudaFuncGetAttributes(&fa, step_q14) == cudaSuccess) stat = fa.sharedSizeBytes;
   else cudaGetLastError();
   return v - (int)align_up((int)stat + 64, 128);
+}
+
+// Step kernel of a launch: the 96-register form, or the 80-register form
+// (_r80) when the grid spans more than one wave of the 96-register form and
+// the lower cap raises the CTAs resident per SM.  The shared-memory limit
+// of every step kernel is raised once per device; the last decision per
+// device is kept, so a repeated configuration costs no occupancy query
+// (the allocation-free entry point calls this every step).
+constexpr int kMaxPickDevices = 64;
+struct PickMemo {
+  int model, npos, threads, smem, nTiles;
+  StepFn fn;
+};
+std::mutex g_pick_mu;
+bool g_step_attr[kMaxPickDevices] = {false};
+PickMemo g_pick_memo[kMaxPickDevices] = {};
+
+int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, StepFn* out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxPickDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_pick_mu);
+  if (!g_step_attr[dev]) {
+    const int lim = max_smem_optin();
+    const StepFn fns[8] = {step_u8,     step_u14,     step_q8,     step_q14,
+                           step_u8_r80, step_u14_r80, step_q8_r80, step_q14_r80};
+    for (StepFn f : fns) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    g_step_attr[dev] = true;
+  }
+  PickMemo& m = g_pick_memo[dev];
+  if (m.fn && m.model == model && m.npos == npos && m.threads == threads && m.smem == smem &&
+      m.nTiles == nTiles) {
+    *out = m.fn;
+    return MPPI_OK;
+  }
+  const StepFn hi = pick_kernel(model, npos, false), lo = pick_kernel(model, npos, true);
+  int occ_hi = 0, occ_lo = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_hi, hi, threads, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_lo, lo, threads, smem));
+  const StepFn fn = (occ_lo > occ_hi && (long)nTiles > (long)occ_hi * num_sms()) ? lo : hi;
+  m = PickMemo{model, npos, threads, smem, nTiles, fn};
+  *out = fn;
+  return MPPI_OK;
 }
 
 }  // namespace
@@ -455,11 +499,11 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   }
   c->last = c->own;
   fill_desc(c);
-  c->fn = pick_kernel(p->model, c->tl.positions_per_thread);
-  if (cudaFuncSetAttribute(c->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_optin()) !=
-      cudaSuccess) {
+  rc = choose_step_kernel(p->model, c->tl.positions_per_thread, c->tl.threads, c->smem, nTiles,
+                          &c->fn);
+  if (rc) {
     free_ctx(c);
-    return fail(MPPI_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
   }
   // initial state: U, S_e = mu ln(e + 0) (Eq. 10 with C_B = 0), first call
   DevState st;
@@ -517,8 +561,12 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
   }
   if (t.samples_per_cta != c->tl.samples_per_cta)
     return fail(MPPI_EINVAL, "obstacle set too large for the controller's tile shape");
+  StepFn fn = nullptr;
+  rc = choose_step_kernel(c->p.model, t.positions_per_thread, t.threads, smem, c->D.nTiles, &fn);
+  if (rc) return rc;
   c->tl = t;
   c->smem = smem;
+  c->fn = fn;
   c->D.J = J;
   c->D.obst = c->d_obst;
   return MPPI_OK;
@@ -776,9 +824,6 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
     // set-up, once per device, with that device current
     void* base = nullptr;
     CK(cudaGetSymbolAddress(&base, g_static_scratch));
-    const int lim = max_smem_optin();
-    const StepFn fns[4] = {step_u8, step_u14, step_q8, step_q14};
-    for (StepFn f : fns) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     g_static_base[dev] = (unsigned char*)base;
   }
   unsigned char* base = g_static_base[dev];
@@ -791,6 +836,9 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   const int nTiles = (K + c.tl.samples_per_cta - 1) / c.tl.samples_per_cta;
   const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
+  StepFn fn = nullptr;  // picked before anything is launched
+  rc = choose_step_kernel(p->model, c.tl.positions_per_thread, c.tl.threads, c.smem, nTiles, &fn);
+  if (rc) return rc;
   size_t off = 0;
   const size_t o_st = carve(&off, sizeof(DevState));
   const size_t o_cU = carve(&off, sizeof(float2) * T);
@@ -830,7 +878,6 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
     CK(cudaMemcpyAsync(c.d_obst, d_obst, sizeof(double) * 3 * J, cudaMemcpyDeviceToDevice, s));
   static_prologue<<<1, 256, 0, s>>>(c.D, d_ctl, 2 * (nGroups + 1));
   CK(cudaGetLastError());
-  StepFn fn = pick_kernel(p->model, c.tl.positions_per_thread);
   fn<<<c.D.nTiles, c.tl.threads, c.smem, s>>>(c.D, d_x0, d_xref);
   CK(cudaGetLastError());
   static_epilogue<<<1, 32, 0, s>>>(c.d_st, d_ctl, d_u0);

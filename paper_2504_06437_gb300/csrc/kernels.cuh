@@ -15,6 +15,15 @@ namespace dbm {
 #define DBM_STEP_MAXNREG 96
 #endif
 
+// Register cap of the second form of the step kernels (suffix _r80), taken
+// for grids of several waves when it raises the CTAs resident per SM: 80
+// lets six 128-thread CTAs share an SM (24 warps instead of 20), which hides
+// more of the barrier loop's pipe latency.  It spills a little, so the
+// 96-register form stays the choice for single-wave grids.
+#ifndef DBM_STEP_MAXNREG_R80
+#define DBM_STEP_MAXNREG_R80 80
+#endif
+
 // One step of one controller: one CTA per tile (MODEL: 0 unicycle,
 // 1 planar quadrotor; 8 or 14 world points per barrier thread).
 __global__ void step_u8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
@@ -25,6 +34,14 @@ __global__ void step_q8(const __grid_constant__ CtrlDesc D, const double* __rest
                         const double* __restrict__ xref);
 __global__ void step_q14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                          const double* __restrict__ xref);
+__global__ void step_u8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                            const double* __restrict__ xref);
+__global__ void step_u14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_q8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                            const double* __restrict__ xref);
+__global__ void step_q14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
 
 // Batched step: persistent CTAs pull (controller, tile) work items.
 struct WorkItem {
