@@ -300,7 +300,7 @@ void free_ctx(mppi_ctx* c) {
 // least twice when K allows, then shrunk until the tile's shared memory
 // (whole-horizon poses and controls, obstacles) fits.
 int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tiling* out,
-                  int* smem_out) {
+                  int* smem_out, bool batched = false) {
   const int sms = num_sms();
   const int n = state_dim(p->model);
   mppi_tiling t = {0, 0, 0, 0};
@@ -326,7 +326,8 @@ int choose_tiling(const mppi_params* p, const mppi_tiling* req, int J, mppi_tili
     const int GT = group_size(nTiles);
     const int nGroups = (nTiles + GT - 1) / GT;
     const int nscl = GT > nGroups ? GT : nGroups;
-    SmemLayout L = smem_layout(p->T, t.samples_per_cta, p->n_shape, J, n, nscl, t.threads / 32);
+    SmemLayout L =
+        smem_layout(p->T, t.samples_per_cta, p->n_shape, J, n, nscl, t.threads / 32, batched);
     if (L.total <= limit) {
       *smem_out = L.total;
       break;
@@ -1216,7 +1217,7 @@ int mppi_batch_add(mppi_batch* b, const mppi_params* p, const double* u_init,
   if (req.samples_per_cta <= 0) req.samples_per_cta = 32;
   if (req.samples_per_cta > p->K) req.samples_per_cta = p->K;
   int smem = 0;
-  rc = choose_tiling(p, &req, J, &s.tl, &smem);
+  rc = choose_tiling(p, &req, J, &s.tl, &smem, true);
   if (rc) return rc;
   if (smem > batch_max_smem(b)) return fail(MPPI_EINVAL, "controller too large for the batch kernel");
   s.J = J;
@@ -1276,7 +1277,7 @@ int mppi_batch_set_obstacles(mppi_batch* b, int32_t slot, const double* cxcyr, i
   BatchSlot& s = b->slots[slot];
   mppi_tiling t;
   int smem = 0;
-  int rc = choose_tiling(&s.p, &s.tl, J, &t, &smem);
+  int rc = choose_tiling(&s.p, &s.tl, J, &t, &smem, true);
   if (rc) return rc;
   if (smem > batch_max_smem(b)) return fail(MPPI_EINVAL, "obstacle set too large");
   if (b->lane.last) CK(cudaStreamSynchronize(b->lane.last));

@@ -37,12 +37,12 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const CtrlDesc* __
     const double* x0 = inputs + e.x0_off;
     const double* xref = inputs + e.xref_off;
     double* uo = u0_out + 8 * w.ctrl;  // u0 and the predicted next state
-    // one-batch merge: see merge_partials
+    // the batched form of the tile: see run_tile
     switch (Ds.model * 2 + npos_code(Ds.NPOS)) {
-      case 0: run_tile<0, 8, false>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
-      case 1: run_tile<0, 14, false>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
-      case 2: run_tile<1, 8, false>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
-      default: run_tile<1, 14, false>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
+      case 0: run_tile<0, 8, true>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
+      case 1: run_tile<0, 14, true>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
+      case 2: run_tile<1, 8, true>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
+      default: run_tile<1, 14, true>(Ds, w.tile, x0, xref, smem, ts, phase, uo); break;
     }
     __syncthreads();  // Ds and s_item are reused by the next item
   }

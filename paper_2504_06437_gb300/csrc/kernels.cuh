@@ -72,7 +72,7 @@ __device__ __forceinline__ void step_body(const CtrlDesc& D, const double* __res
   if (threadIdx.x == 0) mbar_init(&ts.mbar);
   __syncthreads();
   uint32_t phase = 0u;
-  run_tile<MODEL, NPOS, true>(D, blockIdx.x, x0, xref, smem, ts, phase);
+  run_tile<MODEL, NPOS, false>(D, blockIdx.x, x0, xref, smem, ts, phase);
 }
 
 }  // namespace dbm

@@ -133,15 +133,26 @@ __host__ __device__ inline int merge_buf_bytes(int ncol, int nthreads) {
   return align_up(8 * merge_row_groups(ncol, nthreads) * (ncol + 1), 16);  // + Z
 }
 
+// Row stride of the tile's (step, sample) arrays (poses, clamped controls,
+// unit sums): element (t, s) sits at t SP + s.  The rollout scans and the
+// per-sample cost loops step through a sample's row with lanes on
+// consecutive t, so an even S folds the lanes' float4 and float2 accesses
+// onto a few banks (S = 32: all onto one).  The persistent batch kernel
+// rounds SP up to an odd number, which spreads them (a 64-controller mix
+// at S = 32: 3.31 -> 3.00 ms); the one-controller kernels keep SP = S,
+// which measured faster there (their autotuned S avoid the worst strides).
+__host__ __device__ inline int row_stride(int S, bool batched) { return batched ? (S | 1) : S; }
+
 __host__ __device__ inline SmemLayout smem_layout(int T, int S, int P, int J, int n, int nscl,
-                                                  int nwarps) {
+                                                  int nwarps, bool batched) {
   SmemLayout L;
   int off = 0;
   L.obs4 = off;
   off += 16 * (J > 0 ? J : 1);
   off = align_up(off, 16);
   L.region = off;
-  int main_b = 16 * T * S + 8 * T * S;
+  const int SP = row_stride(S, batched);
+  int main_b = 16 * T * SP + 8 * T * SP;
   int raw_b = align_up(24 * J, 16);
   int nom_b = 16 * T + 4 * T * P;
   int merge_b = merge_buf_bytes(2 * T, 32 * nwarps) + 8 * (nscl > 1 ? nscl : 1);
@@ -150,7 +161,7 @@ __host__ __device__ inline SmemLayout smem_layout(int T, int S, int P, int J, in
   if (nom_b > reg) reg = nom_b;
   if (merge_b > reg) reg = merge_b;
   L.pose = off;
-  L.V = off + 16 * T * S;
+  L.V = off + 16 * T * SP;
   off += align_up(reg, 16);
   L.red = off;
   off += 8 * 4 * 32;
@@ -380,8 +391,9 @@ struct TileScratch {
   unsigned long long iter;             // iteration counter of this step
 };
 
-// Fused barrier over nunits (step, sample) units; unit u has pose pose[u]
-// and P shape points shp[0..P).  Each thread takes NPOS / P whole units at a
+// Fused barrier over nunits = T S (step, sample) units; unit u = t S + s has
+// its pose at pose[t SP + s] (SP = row_stride(S, BATCHED)) and P shape
+// points shp[0..P).  Each thread takes NPOS / P whole units at a
 // time (NPOS >= P), units base + k nthreads + tid (k < NPOS / P) so that
 // neighbouring lanes read neighbouring poses, keeps their world points in
 // registers and streams every
@@ -396,11 +408,20 @@ struct TileScratch {
 // uB[u * ustride]; the sign bit of hi marks a unit in which some h <= 0
 // (collision).  A thread reads the poses of its units before it writes their
 // sums, so uB may overlay pose.
-template <int NPOS>
-__device__ __forceinline__ void barrier_units(int nunits, int P, int J, const float4* pose,
+template <int NPOS, bool BATCHED>
+__device__ __forceinline__ void barrier_units(int nunits, int S, int P, int J, const float4* pose,
                                               const float2* __restrict__ shp,
                                               const float4* __restrict__ obs4, float h_eps,
                                               float2* uB, int ustride, int tid, int nthreads) {
+  // unit u = t S + s lives at t SP + s = u + (SP - S) floor(u / S); the
+  // quotient by one multiply-high with m = ceil(2^32 / S), exact while
+  // u (m S - 2^32) < 2^32 (here u < T S <= 2^13 and m S - 2^32 < S <= 32)
+  const unsigned pad = (unsigned)(row_stride(S, BATCHED) - S);
+  const unsigned mS = pad ? 0xffffffffu / (unsigned)S + 1u : 0u;
+  auto at = [&](int u) {
+    if constexpr (BATCHED) return (int)((unsigned)u + pad * __umulhi((unsigned)u, mS));
+    else return u;
+  };
   static_assert(NPOS % 2 == 0, "points are held in packed pairs");
   constexpr int NP2 = NPOS / 2;
   const int upt = NPOS / P;  // units per thread per round
@@ -413,7 +434,7 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
     for (int i = 0; i < NPOS; ++i) {
       const int u = ub + uu * nthreads;
       const bool ok = (i < used) && (u < nunits);
-      const float4 ps = pose[ok ? u : ub];
+      const float4 ps = pose[at(ok ? u : ub)];
       const float2 sh = shp[ok ? p : 0];
       const float X = fmaf(ps.z, sh.x, fmaf(-ps.w, sh.y, ps.x));
       const float Y = fmaf(ps.w, sh.x, fmaf(ps.z, sh.y, ps.y));
@@ -483,7 +504,7 @@ __device__ __forceinline__ void barrier_units(int nunits, int P, int J, const fl
         coll |= (mn[i] <= 0.0f);
         if (++p == P) {
           const int u = ub + uu * nthreads;
-          if (u < nunits) uB[(size_t)u * ustride] = make_float2(coll ? -f.hi : f.hi, f.lo);
+          if (u < nunits) uB[(size_t)at(u) * ustride] = make_float2(coll ? -f.hi : f.hi, f.lo);
           f.hi = 0.0f;
           f.lo = 0.0f;
           coll = false;

@@ -331,8 +331,11 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 
 // One tile of one controller.  ts.mbar must be initialised; mbar_phase is
 // each thread's own copy of the parity of the barrier's next completion.
-// PIPELINED_MERGE selects the form of merge_partials (the same result).
-template <int MODEL, int NPOS, bool PIPELINED_MERGE>
+// BATCHED: the tile runs in the persistent batch kernel, which takes the
+// one-batch form of merge_partials and the odd row stride of row_stride;
+// the one-controller kernels take the pipelined merge and SP = S.  Both
+// choices were measured per kernel; the results are the same bit for bit.
+template <int MODEL, int NPOS, bool BATCHED>
 __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
                          const double* __restrict__ xrefg, char* smem, TileScratch& ts,
                          uint32_t& mbar_phase, double* u0_out = nullptr) {
@@ -340,7 +343,8 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
   const int T = D.T, S = D.S, P = D.P, J = D.J, K = D.K;
-  const SmemLayout L = smem_layout(T, S, P, J, n, D.nscl, nwarps);
+  const int SP = row_stride(S, BATCHED);  // row stride of the (t, s) arrays
+  const SmemLayout L = smem_layout(T, S, P, J, n, D.nscl, nwarps, BATCHED);
   float4* obs4 = reinterpret_cast<float4*>(smem + L.obs4);
   float4* pose = reinterpret_cast<float4*>(smem + L.pose);
   float2* uB = reinterpret_cast<float2*>(smem + L.pose);  // overlays pose, stride 2
@@ -465,7 +469,8 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     const uint32_t it_hi = (uint32_t)(st->iter >> 32);
     const float L00 = st->L00, L10 = st->L10, L11 = st->L11;
     const float lo0 = D.umin[0], hi0 = D.umax[0], lo1 = D.umin[1], hi1 = D.umax[1];
-    // item i = t S + s; (t, s) stepped by nthreads without a division
+    // item i = t S + s, stored at t SP + s; (t, s) stepped by nthreads
+    // without a division
     const int dt = nthreads / S, ds = nthreads - dt * S;
     int t = tid / S, s = tid - t * S;
 #pragma unroll 2
@@ -474,7 +479,8 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
                                     D.key0, D.key1);
       const float2 du = nln_draw(r, L00, L10, L11, D.ln_mu, D.ln_sigma);
       const float2 u = Uf[t];
-      V[i] = make_float2(fminf(fmaxf(u.x + du.x, lo0), hi0), fminf(fmaxf(u.y + du.y, lo1), hi1));
+      V[t * SP + s] =
+          make_float2(fminf(fmaxf(u.x + du.x, lo0), hi0), fminf(fmaxf(u.y + du.y, lo1), hi1));
       t += dt;
       s += ds;
       if (s >= S) {
@@ -503,7 +509,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   // ---- dynamics and stage/control costs: one warp per sample
   for (int s = warp; s < S; s += nwarps) {
     FF c = {0.0f, 0.0f};
-    scan_trajectory<MODEL, true>(D, T, V + s, S, xi, pose + s, S, Uf, Af, xrf, c, lane);
+    scan_trajectory<MODEL, true>(D, T, V + s, SP, xi, pose + s, SP, Uf, Af, xrf, c, lane);
     c = warp_sum_ff(c);
     if (lane == 0) {
       scH[s] = c.hi;
@@ -513,7 +519,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   __syncthreads();
 
   // ---- fused barrier over all (step, sample) units, sums over the poses
-  barrier_units<NPOS>(T * S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid, nthreads);
+  barrier_units<NPOS, BATCHED>(T * S, S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid, nthreads);
   __syncthreads();
 
   // ---- barrier-state and collision costs: one warp per sample; costs are
@@ -525,7 +531,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     FF b = {0.0f, 0.0f};
     bool coll = false;
     for (int t = lane; t < T; t += 32) {
-      const float2 v = uB[2 * (t * S + s)];
+      const float2 v = uB[2 * (t * SP + s)];
       const bool cl = __float_as_int(v.x) < 0;
       ff_add_prod(b, cw[t], fabsf(v.x), v.y);
       if (cl) ff_add(b, D.C_coll);
@@ -567,7 +573,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     float* prow = D.part + (size_t)tile * 2 * T;
     for (int c = tid; c < 2 * T; c += nthreads) {
       const int t = c >> 1;
-      const float* Vt = reinterpret_cast<const float*>(V + t * S) + (c & 1);
+      const float* Vt = reinterpret_cast<const float*>(V + t * SP) + (c & 1);
       const float u = reinterpret_cast<const float*>(Uf + t)[c & 1];
       float a = 0.0f;
       for (int s = 0; s < S; ++s) a = fmaf(eS[s], Vt[2 * s] - u, a);
@@ -603,7 +609,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   const int ncol = 2 * T;
   FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
   float2* zi = reinterpret_cast<float2*>(smem + L.region + merge_buf_bytes(ncol, nthreads));
-  merge_partials<PIPELINED_MERGE>(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
+  merge_partials<!BATCHED>(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
                  D.inv_lambda_f, scl, zi, mbuf, &ts.Z, col_hi, col_lo, tid, nthreads);
   if (D.nGroups > 1) {
     for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
@@ -624,7 +630,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     }
     __syncthreads();
     if (!ts.flag) return;
-    merge_partials<PIPELINED_MERGE>(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
+    merge_partials<!BATCHED>(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
                    &ts.Z, col_hi, col_lo, tid, nthreads);
   }
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
