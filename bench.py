@@ -45,10 +45,13 @@ def algorithmic_ops(K, T, P, J):
 
 
 def kernel_src_sha():
+    """Hash of the device code of the step and batch kernels (the kernel
+    translation units k_*.cu and the device headers), not of the host
+    runtime: the key of the committed traffic counters."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2504_06437_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith(".cuh") or (f.startswith("k_") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -151,8 +151,9 @@ int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h);
 
 /* Autotuner: runs the step of this problem (params, obstacle set) under
  * each candidate launch shape -- samples per CTA, threads per CTA, world
- * points per barrier thread -- on scratch controllers, `iters` timed steps
- * each (CUDA events), and returns the fastest in *best and its time per step
+ * points per barrier thread -- on scratch controllers, at least `iters` timed
+ * steps each and enough to cover about 2 ms of device time (CUDA events),
+ * and returns the fastest in *best and its time per step
  * in microseconds in *best_us (may be NULL).  Allocates and frees its own
  * scratch controllers; synchronises.  Errors: MPPI_EINVAL, MPPI_ECUDA (no
  * candidate ran). */

@@ -891,10 +891,14 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
 // the fastest.  Candidates: samples per CTA in {2, 4, 5, 7, 8, 10, 11, 12, 13,
 // 14, 16, 20, 24, 27, 32} (those giving at most 16 CTAs per SM; neighbouring
 // values change how the last wave of CTAs fills the SMs), threads in
-// {128, 256, 512}, world points per barrier thread in {8, 14} (whole units).  Each candidate runs
-// `iters` steps after two warm-up steps on a scratch controller, timed with
-// CUDA events; the controller state is reset so every candidate sees the same
-// inputs.
+// {128, 256, 512}, world points per barrier thread in {8, 14} (whole units).
+// Each candidate runs on a scratch controller: two warm-up steps, two steps
+// that estimate its step time, then max(iters, steps filling about 2 ms)
+// timed steps (CUDA events).  The controller state is reset so every
+// candidate sees the same inputs.
+constexpr float kTuneWindowUs = 2000.0f;  // device time timed per candidate, at least
+constexpr int kTuneMaxReps = 400;
+
 extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J, int32_t iters,
                              mppi_tiling* best, float* best_us) {
   int rc = validate(p);
@@ -932,21 +936,31 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
         bool ok = true;
         for (int w = 0; w < 2 && ok; ++w) ok = mppi_step(c, x0, x0 + n, nullptr) == MPPI_OK;
         if (ok) ok = cudaStreamSynchronize(c->own) == cudaSuccess;
+        // timed steps: at least `iters`, and enough to cover kTuneWindowUs of
+        // device time (estimated from two steps), so that microsecond-scale
+        // steps are not ranked on launch jitter
+        int reps = iters;
         float ms = 0.0f;
-        if (ok) {
+        for (int pass = 0; pass < 2 && ok; ++pass) {
+          const int k = pass == 0 ? 2 : reps;
           cudaEventRecord(e0, c->own);
-          for (int i = 0; i < iters && ok; ++i)
+          for (int i = 0; i < k && ok; ++i)
             ok = mppi_step_device(c, c->d_in, c->d_in + n, nullptr) == MPPI_OK;
           cudaEventRecord(e1, c->own);
           ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
           if (ok) cudaEventElapsedTime(&ms, e0, e1);
+          if (pass == 0 && ok) {
+            const float est_us = 1000.0f * ms / 2.0f;
+            const float want = est_us > 0.0f ? kTuneWindowUs / est_us : (float)kTuneMaxReps;
+            reps = std::max(iters, std::min(kTuneMaxReps, (int)want + 1));
+          }
         }
         mppi_destroy(c);
         if (!ok) {
           cudaGetLastError();
           continue;
         }
-        const float us = 1000.0f * ms / iters;
+        const float us = 1000.0f * ms / reps;
         if (us < best_t) {
           best_t = us;
           best_tl = t;
