@@ -888,10 +888,12 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
 
 // ------------------------------------------------------------------------
 // Autotuner: time the candidate launch shapes on the problem itself and keep
-// the fastest.  Candidates: samples per CTA in {2, 4, 5, 7, 8, 10, 11, 12, 13,
-// 14, 16, 20, 24, 27, 32} (those giving at most 16 CTAs per SM; neighbouring
-// values change how the last wave of CTAs fills the SMs), threads in
-// {128, 256, 512}, world points per barrier thread in {8, 14} (whole units).
+// the fastest.  Candidates: every samples-per-CTA value 1..32 (those giving
+// at most 16 CTAs per SM): neighbouring values trade how the last wave of
+// CTAs fills the SMs against how fully the tile's units fill the barrier's
+// register slots, a discrete trade-off settled here by measurement; threads
+// in {128, 256, 512}; world points per barrier thread in {8, 14} (whole
+// units).
 // Each candidate runs on a scratch controller: two warm-up steps, two steps
 // that estimate its step time, then max(iters, steps filling about 2 ms)
 // timed steps (CUDA events).  The controller state is reset so every
@@ -906,7 +908,8 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
   if (!best) return fail(MPPI_EINVAL, "best is NULL");
   if (iters < 1) iters = 5;
   const int sms = num_sms();
-  const int S_opts[] = {2, 4, 5, 7, 8, 10, 11, 12, 13, 14, 16, 20, 24, 27, 32};
+  int S_opts[32];
+  for (int i = 0; i < 32; ++i) S_opts[i] = i + 1;
   const int NT_opts[3] = {128, 256, 512};
   const int NP_opts[2] = {8, 14};
   const int n = state_dim(p->model);
