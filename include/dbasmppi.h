@@ -163,6 +163,14 @@ int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J,
 /* The launch shape in use and the number of CTAs of one step. */
 int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas);
 
+/* Register cap of the step kernel the context launches: 96, or 80 when the
+ * grid spans more than one wave of the 96-register form and the lower cap
+ * adds resident CTAs per SM (re-chosen on create and on a new obstacle
+ * set).  Both forms compute the same results bit for bit.  A library
+ * choice with no counterpart in the paper.  Errors: MPPI_ESTATE (NULL
+ * context), MPPI_EINVAL (NULL output). */
+int mppi_get_kernel_regs(mppi_ctx* c, int32_t* regs_cap);
+
 /* Checkpoint / resume of the per-controller state: U (T x 2), S_e, beta,
  * first-call flag, iteration counter.  Restoring a state reproduces the
  * following steps exactly, since the generator is counter-based. */

@@ -122,6 +122,7 @@ def load():
     lib.mppi_get_debug.argtypes = [vp, _dp, C.POINTER(C.c_uint8), _dp, _dp, _dp]
     lib.mppi_io_bytes.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     lib.mppi_get_tiling.argtypes = [vp, C.POINTER(Tiling), C.POINTER(C.c_int32)]
+    lib.mppi_get_kernel_regs.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.mppi_get_state.argtypes = [vp, _dp, _dp, _dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
     lib.mppi_set_state.argtypes = [vp, _dp, C.c_double, C.c_double, C.c_int32, C.c_uint64]
     lib.mppi_destroy.argtypes = [vp]
@@ -304,6 +305,12 @@ class Controller:
         return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
                     positions_per_thread=t.positions_per_thread, chunk_steps=t.chunk_steps,
                     n_ctas=n.value)
+
+    def kernel_regs(self) -> int:
+        """Register cap of the step kernel this controller launches (96 or 80)."""
+        r = C.c_int32()
+        _check(load().mppi_get_kernel_regs(self.h, C.byref(r)))
+        return r.value
 
     def io_bytes(self):
         a, b = C.c_uint64(), C.c_uint64()

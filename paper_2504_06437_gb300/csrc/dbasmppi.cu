@@ -664,6 +664,15 @@ int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas) {
   return MPPI_OK;
 }
 
+int mppi_get_kernel_regs(mppi_ctx* c, int32_t* regs_cap) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!regs_cap) return fail(MPPI_EINVAL, "regs_cap is NULL");
+  const bool r80 = c->fn == step_u8_r80 || c->fn == step_u14_r80 || c->fn == step_q8_r80 ||
+                   c->fn == step_q14_r80;
+  *regs_cap = r80 ? DBM_STEP_MAXNREG_R80 : DBM_STEP_MAXNREG;
+  return MPPI_OK;
+}
+
 int mppi_get_state(mppi_ctx* c, double* U, double* S_e, double* beta, int32_t* first,
                    uint64_t* iter) {
   if (!c) return fail(MPPI_ESTATE, "context is NULL");

@@ -164,3 +164,33 @@ def test_batch_autotuned_policy_shapes_and_equals_alone(gpu):
                 g.set_obstacles(w.obstacles)
                 g.step(w.x_start, w.reference(w.x_start))
                 np.testing.assert_array_equal(u_b[i], g.get_control())
+
+
+def test_register_forms_equal_bitwise(gpu):
+    """A controller whose grid spans several waves runs the 80-register form
+    of the step kernel; a one-wave controller the 96-register form.  The
+    80-register controller gives, bit for bit, what the batch kernel gives
+    for it at the same launch shape (and the batch kernel equals the
+    96-register form in the test above)."""
+    w = W.unicycle_stress(3, K=16384, T=40)
+    shape = dict(samples_per_cta=20, threads=256, positions_per_thread=8)
+    small = W.unicycle_stress(3, K=512, T=40)
+    with gpu.Controller(small.params, tiling=shape) as g:
+        g.set_obstacles(small.obstacles)
+        assert g.kernel_regs() == 96
+    with gpu.Batch(4, 256 << 20) as b, gpu.Controller(w.params, tiling=shape) as g:
+        g.set_obstacles(w.obstacles)
+        assert g.tiling()["n_ctas"] == (16384 + 19) // 20
+        assert g.kernel_regs() == 80
+        slot = b.add(w.params, w.obstacles, tiling=shape)
+        for _ in range(2):
+            xr = w.reference(w.x_start)
+            b.step([slot], [w.x_start], [xr])
+            u_b = b.controls()
+            st = b.state(slot)
+            g.step(w.x_start, xr)
+            u0, U = g.get_control(want_U=True)
+            d = g.get_debug()
+            np.testing.assert_array_equal(u_b[0], u0)
+            np.testing.assert_array_equal(st["U"], U)
+            np.testing.assert_array_equal(st["costs"], d["costs"])
