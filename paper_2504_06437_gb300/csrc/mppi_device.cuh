@@ -14,10 +14,11 @@
 //   barrier    all threads evaluate the fused barrier sum over every
 //              (step, sample) unit, its P shape points and every obstacle
 //              (Eq. 5, 13/15): each thread keeps whole units (NPOS world
-//              points) in registers, streams the obstacle set from shared
-//              memory (broadcast reads), adds two obstacles per approximate
-//              reciprocal, and sums each unit's points exactly into a float
-//              pair, written over the unit's pose;
+//              points) in registers as packed pairs, streams the obstacle
+//              set from shared memory (broadcast reads), evaluates two points
+//              per packed two-lane FP32 instruction, adds two obstacles per
+//              approximate reciprocal, and sums each unit's points exactly
+//              into a float pair, written over the unit's pose;
 //   costs      one warp per sample adds the barrier-state and collision costs;
 //   partials   the tile's minimum cost, its exponentiated weights, their sum Z
 //              and the 2T weighted column sums of the perturbations (Eq. 4);
@@ -25,6 +26,10 @@
 //              the partials log-sum-exp style against the exact minimum over
 //              the tiles, then runs the final stage (U*, nominal rollout, S_e,
 //              shift).
+// The one-controller kernels exist in a 96- and an 80-register form (the
+// host picks per launch); the batch kernel's tiles take a padded row stride
+// and the one-batch merge (BATCHED in run_tile).  All forms give the same
+// results bit for bit.
 // The DBaS recursion of Eq. 7, w_t = b_t + gamma (w_{t-1} - beta_d), is
 // linear, so its cost sum is evaluated in unrolled form:
 //   sum_{t=1..T} w_t = sum_s c_s b_s + beta_0 g1 - gamma beta_d csum,
