@@ -123,8 +123,13 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J);
 
 /* One iteration from host data.  x0: measured state (n doubles).  xref:
  * (T+1) x n reference, row t compared with x_t (row 0 unused), or NULL for
- * x_goal repeated.  Copies the inputs to the device on the stream and
- * enqueues the step; returns without waiting. */
+ * x_goal repeated.  Copies the inputs into one of two mapped pinned staging
+ * buffers, used in turn, and enqueues the step, whose kernel reads them from
+ * host memory over the host link (no separate copy precedes the launch);
+ * returns without waiting, and the caller's arrays may be reused at once.
+ * A staging buffer is rewritten only after the step that read it has
+ * finished: a third call in a row without a synchronisation waits for the
+ * first step. */
 int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream);
 
 /* One iteration from device data (x0, xref in device memory, same layout;

@@ -247,6 +247,15 @@ class Controller:
             rc = lib.mppi_create(C.byref(self.params), _ptr(u) if u is not None else None, C.byref(h))
         _check(rc)
         self.h = h
+        # per-controller argument buffers with their ctypes pointers made
+        # once: numpy's pointer conversion costs microseconds per call, more
+        # than the rest of a step's host work
+        self._x0b = np.zeros(self.n)
+        self._xrb = np.zeros((self.T + 1, self.n))
+        self._u0b = np.zeros(2)
+        self._Ub = np.zeros((self.T, 2))
+        self._px0, self._pxr = _ptr(self._x0b), _ptr(self._xrb)
+        self._pu0, self._pU = _ptr(self._u0b), _ptr(self._Ub)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -270,20 +279,21 @@ class Controller:
         _check(load().mppi_set_obstacles(self.h, _ptr(ob) if ob.size else None, ob.shape[0]))
 
     def step(self, x0, xref=None, stream=None):
-        x0 = _f64(x0)
-        xr = None if xref is None else _f64(xref).reshape(self.T + 1, self.n)
-        _check(load().mppi_step(self.h, _ptr(x0), _ptr(xr) if xr is not None else None,
-                                _stream_ptr(stream)))
+        self._x0b[:] = x0
+        pxr = None
+        if xref is not None:
+            self._xrb[...] = np.asarray(xref, dtype=np.float64).reshape(self.T + 1, self.n)
+            pxr = self._pxr
+        _check(load().mppi_step(self.h, self._px0, pxr, _stream_ptr(stream)))
 
     def step_device(self, d_x0: int, d_xref: int, stream=None):
         _check(load().mppi_step_device(self.h, C.c_void_p(d_x0), C.c_void_p(d_xref),
                                        _stream_ptr(stream)))
 
     def get_control(self, want_U: bool = False):
-        u0 = np.zeros(2)
-        U = np.zeros((self.T, 2)) if want_U else None
-        _check(load().mppi_get_control(self.h, _ptr(u0), _ptr(U) if want_U else None))
-        return (u0, U) if want_U else u0
+        _check(load().mppi_get_control(self.h, self._pu0, self._pU if want_U else None))
+        u0 = self._u0b.copy()
+        return (u0, self._Ub.copy()) if want_U else u0
 
     def get_debug(self) -> dict:
         K, T = self.K, self.T

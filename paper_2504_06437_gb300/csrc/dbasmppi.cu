@@ -257,13 +257,20 @@ struct mppi_ctx {
   uint8_t* d_coll = nullptr;
   double* d_Ustar = nullptr;
   double* d_w = nullptr;
-  double* h_in = nullptr;   // pinned staging of the inputs
+  // Host inputs of mppi_step: two mapped pinned staging buffers, used in
+  // turn; the kernel reads x0 and xref from them over the host link (their
+  // device aliases in h_in_dev), so no copy is staged before the launch.  A
+  // buffer is rewritten only after the kernel that read it has finished
+  // (in_ev, recorded after that launch).
+  double* h_in[2] = {nullptr, nullptr};
+  double* h_in_dev[2] = {nullptr, nullptr};
+  cudaEvent_t in_ev[2] = {nullptr, nullptr};
+  bool in_ev_pending[2] = {false, false};
+  int in_next = 0;
   DevState* h_st = nullptr; // pinned readback
   double* h_U = nullptr;    // pinned readback
   cudaStream_t own = nullptr;
   cudaStream_t last = nullptr;
-  cudaEvent_t in_ev = nullptr;
-  bool in_ev_pending = false;
   bool stepped = false;
 };
 
@@ -288,10 +295,12 @@ void free_ctx(mppi_ctx* c) {
   cudaFree(c->d_coll);
   cudaFree(c->d_Ustar);
   cudaFree(c->d_w);
-  cudaFreeHost(c->h_in);
+  for (int b = 0; b < 2; ++b) {
+    cudaFreeHost(c->h_in[b]);
+    if (c->in_ev[b]) cudaEventDestroy(c->in_ev[b]);
+  }
   cudaFreeHost(c->h_st);
   cudaFreeHost(c->h_U);
-  if (c->in_ev) cudaEventDestroy(c->in_ev);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
 }
@@ -486,15 +495,24 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   ALLOC(c->d_Ustar, sizeof(double) * 2 * T);
   ALLOC(c->d_w, sizeof(double) * K);
 #undef ALLOC
-  if (cudaMallocHost((void**)&c->h_in, sizeof(double) * (n + (T + 1) * n)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->h_st, sizeof(DevState)) != cudaSuccess ||
+  const size_t in_bytes = sizeof(double) * (n + (T + 1) * n);
+  for (int b = 0; b < 2; ++b) {
+    if (cudaHostAlloc((void**)&c->h_in[b], in_bytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->h_in_dev[b], c->h_in[b], 0) != cudaSuccess) {
+      cudaGetLastError();
+      free_ctx(c);
+      return fail(MPPI_ENOMEM, "mapped pinned host allocation failed");
+    }
+  }
+  if (cudaMallocHost((void**)&c->h_st, sizeof(DevState)) != cudaSuccess ||
       cudaMallocHost((void**)&c->h_U, sizeof(double) * 2 * T) != cudaSuccess) {
     cudaGetLastError();
     free_ctx(c);
     return fail(MPPI_ENOMEM, "pinned host allocation failed");
   }
   if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->in_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->in_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     free_ctx(c);
     return fail(MPPI_ECUDA, "stream/event creation failed");
   }
@@ -591,17 +609,21 @@ int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream) {
   if (!finite_all(x0, n)) return fail(MPPI_EINVAL, "x0 is not finite");
   if (xref && !finite_all(xref, (T + 1) * n)) return fail(MPPI_EINVAL, "xref is not finite");
   cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
-  if (c->in_ev_pending) CK(cudaEventSynchronize(c->in_ev));  // staging buffer free again
-  memcpy(c->h_in, x0, sizeof(double) * n);
+  const int b = c->in_next;
+  if (c->in_ev_pending[b]) CK(cudaEventSynchronize(c->in_ev[b]));  // its reader has finished
+  double* h = c->h_in[b];
+  memcpy(h, x0, sizeof(double) * n);
   if (xref) {
-    memcpy(c->h_in + n, xref, sizeof(double) * (T + 1) * n);
+    memcpy(h + n, xref, sizeof(double) * (T + 1) * n);
   } else {
-    for (int t = 0; t <= T; ++t) memcpy(c->h_in + n + t * n, c->p.x_goal, sizeof(double) * n);
+    for (int t = 0; t <= T; ++t) memcpy(h + n + t * n, c->p.x_goal, sizeof(double) * n);
   }
-  CK(cudaMemcpyAsync(c->d_in, c->h_in, sizeof(double) * (n + (T + 1) * n), cudaMemcpyHostToDevice, s));
-  CK(cudaEventRecord(c->in_ev, s));
-  c->in_ev_pending = true;
-  return mppi_step_device(c, c->d_in, c->d_in + n, s);
+  const int rc = mppi_step_device(c, c->h_in_dev[b], c->h_in_dev[b] + n, s);
+  if (rc) return rc;
+  CK(cudaEventRecord(c->in_ev[b], s));
+  c->in_ev_pending[b] = true;
+  c->in_next = b ^ 1;
+  return MPPI_OK;
 }
 
 int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
@@ -948,6 +970,10 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
         bool ok = true;
         for (int w = 0; w < 2 && ok; ++w) ok = mppi_step(c, x0, x0 + n, nullptr) == MPPI_OK;
         if (ok) ok = cudaStreamSynchronize(c->own) == cudaSuccess;
+        // the timed steps read their inputs from device memory
+        if (ok)
+          ok = cudaMemcpy(c->d_in, x0, sizeof(double) * n * (p->T + 2), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
         // timed steps: at least `iters`, and enough to cover kTuneWindowUs of
         // device time (estimated from two steps), so that microsecond-scale
         // steps are not ranked on launch jitter
