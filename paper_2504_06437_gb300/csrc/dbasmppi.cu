@@ -269,6 +269,8 @@ struct mppi_ctx {
   int in_next = 0;
   DevState* h_st = nullptr; // pinned readback
   double* h_U = nullptr;    // pinned readback
+  HostOut* h_out = nullptr;      // mapped mirror of u0 and status, written by the step
+  HostOut* h_out_dev = nullptr;  // its device alias
   cudaStream_t own = nullptr;
   cudaStream_t last = nullptr;
   bool stepped = false;
@@ -301,6 +303,7 @@ void free_ctx(mppi_ctx* c) {
   }
   cudaFreeHost(c->h_st);
   cudaFreeHost(c->h_U);
+  cudaFreeHost(c->h_out);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
 }
@@ -435,6 +438,7 @@ void fill_desc(mppi_ctx* c) {
   D.costs = c->d_costs;
   D.coll = c->d_coll;
   D.Ustar = c->d_Ustar;
+  D.host_out = c->h_out_dev;  // null for the batch slots and the static entry point
 }
 
 int check_status(mppi_ctx* c) {
@@ -504,6 +508,13 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
       return fail(MPPI_ENOMEM, "mapped pinned host allocation failed");
     }
   }
+  if (cudaHostAlloc((void**)&c->h_out, sizeof(HostOut), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&c->h_out_dev, c->h_out, 0) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(c);
+    return fail(MPPI_ENOMEM, "mapped pinned host allocation failed");
+  }
+  memset(c->h_out, 0, sizeof(HostOut));
   if (cudaMallocHost((void**)&c->h_st, sizeof(DevState)) != cudaSuccess ||
       cudaMallocHost((void**)&c->h_U, sizeof(double) * 2 * T) != cudaSuccess) {
     cudaGetLastError();
@@ -629,14 +640,15 @@ int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream) {
 int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
   if (!c) return fail(MPPI_ESTATE, "context is NULL");
   if (!c->stepped) return fail(MPPI_ESTATE, "no step has run");
-  CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, c->last));
+  // u0 and the status word come from the mapped mirror the step's final
+  // stage wrote; only U, when asked for, is copied
   if (U) CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost, c->last));
   CK(cudaStreamSynchronize(c->last));
-  int rc = check_status(c);
-  if (rc) return rc;
+  if (c->h_out->status == kStatusTimeout)
+    return fail(MPPI_ETIMEOUT, "a bounded device wait (obstacle staging) expired");
   if (u0) {
-    u0[0] = c->h_st->u0[0];
-    u0[1] = c->h_st->u0[1];
+    u0[0] = c->h_out->u0[0];
+    u0[1] = c->h_out->u0[1];
   }
   if (U) memcpy(U, c->h_U, sizeof(double) * 2 * c->p.T);
   return MPPI_OK;

@@ -76,6 +76,15 @@ struct DevState {
   int status;        // kStatus*
 };
 
+// Outputs of a step that the host reads after every step, written by the
+// final stage straight into mapped pinned host memory (one-controller
+// contexts; null elsewhere).
+struct HostOut {
+  double u0[2];  // u*_0
+  int status;    // kStatus*
+  int pad;
+};
+
 // Everything a CTA needs to process one tile of one controller.
 struct CtrlDesc {
   int model, K, T, J, P, n;
@@ -109,6 +118,7 @@ struct CtrlDesc {
   double* costs;             // K
   uint8_t* coll;             // K
   double* Ustar;             // T x 2
+  HostOut* host_out;         // device alias of the host mirror, or null
 };
 
 // Shared-memory layout of one tile; host and device compute it alike.

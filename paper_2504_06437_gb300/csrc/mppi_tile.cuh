@@ -310,6 +310,11 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       st->S_e_used = ts.S_e_used;
       st->u0[0] = us0[0];
       st->u0[1] = us0[1];
+      if (D.host_out) {  // what mppi_get_control reads, straight to host memory
+        D.host_out->u0[0] = us0[0];
+        D.host_out->u0[1] = us0[1];
+        D.host_out->status = *reinterpret_cast<volatile int*>(&st->status);
+      }
       constexpr int n = Dyn<MODEL>::n;
       double xn[6] = {0, 0, 0, 0, 0, 0};
       xn[0] = x0g[0] + (double)x1[0];  // back from the frame centred on x0
