@@ -286,3 +286,25 @@ def test_error_paths(gpu):
         g.step(w.x_start)          # xref NULL -> goal repeated
         u0 = g.get_control()
         assert np.all(np.isfinite(u0))
+
+
+def test_back_to_back_steps_without_sync(gpu):
+    """mppi_step stages its inputs in two mapped host buffers used in turn;
+    the kernel reads them over the host link.  Five steps enqueued without a
+    synchronisation, each from a different measured state, give bit for bit
+    what the same steps give with a synchronisation after each: a staging
+    buffer is never rewritten while a kernel still reads it."""
+    w = W.quad2d(2)
+    xs = [w.x_start + 0.05 * i * np.array([1.0, -0.5, 0.0, 0.1, 0.0, 0.02]) for i in range(5)]
+    refs = [w.reference(x) for x in xs]
+    with gpu.Controller(w.params) as a, gpu.Controller(w.params) as b:
+        a.set_obstacles(w.obstacles)
+        b.set_obstacles(w.obstacles)
+        for x, r in zip(xs, refs):
+            a.step(x, r)
+            ua, Ua = a.get_control(want_U=True)
+        for x, r in zip(xs, refs):
+            b.step(x, r)
+        ub, Ub = b.get_control(want_U=True)
+        np.testing.assert_array_equal(ua, ub)
+        np.testing.assert_array_equal(Ua, Ub)
