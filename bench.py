@@ -207,7 +207,9 @@ def run_reference(args, ws, rank):
     ctl = oracle.new_controller(pp)
     x = world.x_start
     xref = world.reference(x)
-    for _ in range(args.warmup):
+    # at least 10 untimed steps: the oracle's first steps run well below its
+    # steady rate (thread start-up, first touch of its buffers)
+    for _ in range(max(args.warmup, 10)):
         oracle.step(pp, world.obstacles, x, xref, ctl)
     times = []
     for _ in range(args.steps):
