@@ -188,19 +188,33 @@ def test_max_sizes(gpu, orc):
     run_pair(gpu, orc, w, steps=1)
 
 
+def bench_tiling(gpu, w):
+    """The launch shape bench.py times for this workload: the autotuner's
+    pick, made the same way (10 timed steps per candidate at least)."""
+    tiling, _ = gpu.autotune(w.params, w.obstacles, iters=10)
+    return tiling
+
+
 def test_quad_full_size_bench_config(gpu, orc):
     """The benchmark workload (K=4096, T=50, 40 obstacles, 7 shape points) in
-    the launch shape the benchmark uses, all samples compared."""
-    run_pair(gpu, orc, W.quad2d(0), steps=2)
+    the launch shape the benchmark uses (the autotuner's pick) and in the
+    library's default shape, all samples compared."""
+    w = W.quad2d(0)
+    run_pair(gpu, orc, w, steps=2, tiling=bench_tiling(gpu, w))
+    run_pair(gpu, orc, w, steps=1)
 
 
-def test_stress_config_sampled(gpu, orc):
+@pytest.mark.parametrize("shape", ["bench", "default"])
+def test_stress_config_sampled(gpu, orc, shape):
     """K=65536, T=100, 200 obstacles: many tile groups.  Costs of 512 sampled
-    samples against the oracle; weights sum to one; U* within the box."""
+    samples against the oracle; weights sum to one; U* within the box.  Run
+    in the launch shape bench.py times (the autotuner's pick, which takes
+    the 80-register form of the kernel on GB300) and in the default shape."""
     w = W.unicycle_stress(0)
     p = w.params
     ctl = orc.new_controller(p)
-    with gpu.Controller(p) as g:
+    tiling = bench_tiling(gpu, w) if shape == "bench" else None
+    with gpu.Controller(p, tiling=tiling) as g:
         g.set_obstacles(w.obstacles)
         x = w.x_start
         xref = w.reference(x)

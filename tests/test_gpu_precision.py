@@ -1,7 +1,8 @@
 """Precision of the GPU step against the FP64 oracle at the three
 single-controller workload sizes (unicycle K=256 T=30 J=10, planar quadrotor
 K=4096 T=50 J=40 with 7 shape points, unicycle K=65536 T=100 J=200), one step
-each from the same inputs, every sample compared.
+each from the same inputs, every sample compared, in the launch shape that
+bench.py times (the autotuner's pick).
 
 The rollout is FP32; the per-sample costs are float pairs relative to a
 shared base; the weights, their normaliser and the weighted update are
@@ -39,23 +40,29 @@ def gpu():
 
 @pytest.mark.parametrize("name", ["unicycle_small", "quad2d", "unicycle_stress"])
 def test_precision_against_oracle(gpu, orc, name):
+    """In the launch shape bench.py times for the workload (the autotuner's
+    pick)."""
     w = W.PRESETS[name](0)
     p = w.params
     ctl = orc.new_controller(p)
     x = w.x_start
     xref = w.reference(x)
     ro = orc.step(p, w.obstacles, x, xref, ctl)
-    with gpu.Controller(p) as g:
+    tiling, _ = gpu.autotune(p, w.obstacles, iters=10)
+    with gpu.Controller(p, tiling=tiling) as g:
         g.set_obstacles(w.obstacles)
         g.step(x, xref)
         u0, _ = g.get_control(want_U=True)
         dbg = g.get_debug()
+        regs = g.kernel_regs()
     rel = np.abs(dbg["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
     u_err = float(np.abs(dbg["Ustar"] - ro["Ustar"]).max())
     w_err = float(np.abs(dbg["weights"] - ro["weights"]).max())
     sure = np.abs(ro["minh"]) > H_MARGIN
     mismatch = int(np.sum((ro["coll"] != dbg["coll"]) & sure))
     rec = dict(workload=name, K=int(p["K"]), T=int(p["T"]), J=int(w.obstacles.shape[0]),
+               tiling=[tiling["samples_per_cta"], tiling["threads"], tiling["positions_per_thread"]],
+               kernel_regs=regs,
                cost_rel_max=float(rel.max()), cost_rel_p99=float(np.quantile(rel, 0.99)),
                u_star_abs_max=u_err, u0_abs_max=float(np.abs(u0 - ro["u0"]).max()),
                weight_abs_max=w_err, weight_sum_minus_1=float(dbg["weights"].sum() - 1.0),
