@@ -153,8 +153,10 @@ int mppi_get_control(mppi_ctx* c, double* u0, double* U);
 int mppi_get_debug(mppi_ctx* c, double* costs, uint8_t* collided,
                    double* weights, double* Ustar, double* scalars);
 
-/* Bytes one mppi_step() copies host -> device (x0 and xref) and one
- * mppi_get_control(c, u0, NULL) copies device -> host. */
+/* Bytes one mppi_step() moves host -> device (x0 and xref, read by the
+ * kernel from the mapped staging) and device -> host for one
+ * mppi_get_control(c, u0, NULL) (u0 and the status word, written by the
+ * step into the mapped mirror). */
 int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h);
 
 /* Autotuner: runs the step of this problem (params, obstacle set) under

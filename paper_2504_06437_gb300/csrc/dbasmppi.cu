@@ -687,7 +687,7 @@ int mppi_get_debug(mppi_ctx* c, double* costs, uint8_t* collided, double* weight
 int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h) {
   if (!c) return fail(MPPI_ESTATE, "context is NULL");
   if (h2d) *h2d = sizeof(double) * (uint64_t)(c->n + (c->p.T + 1) * c->n);
-  if (d2h) *d2h = sizeof(DevState);
+  if (d2h) *d2h = sizeof(HostOut);  // u0 and the status word, written by the step
   return MPPI_OK;
 }
 
