@@ -166,15 +166,21 @@ def test_batch_autotuned_policy_shapes_and_equals_alone(gpu):
                 np.testing.assert_array_equal(u_b[i], g.get_control())
 
 
-def test_register_forms_equal_bitwise(gpu):
+@pytest.mark.parametrize("model,npos", [("unicycle", 8), ("unicycle", 14), ("quad", 8), ("quad", 14)])
+def test_register_forms_equal_bitwise(gpu, model, npos):
     """A controller whose grid spans several waves runs the 80-register form
     of the step kernel; a one-wave controller the 96-register form.  The
     80-register controller gives, bit for bit, what the batch kernel gives
     for it at the same launch shape (and the batch kernel equals the
-    96-register form in the test above)."""
-    w = W.unicycle_stress(3, K=16384, T=40)
-    shape = dict(samples_per_cta=20, threads=256, positions_per_thread=8)
-    small = W.unicycle_stress(3, K=512, T=40)
+    96-register form in the test above).  Both models, 8 and 14 points per
+    barrier thread."""
+    if model == "unicycle":
+        w = W.unicycle_stress(3, K=16384, T=40)
+        small = W.unicycle_stress(3, K=512, T=40)
+    else:
+        w = W.quad2d(3, K=16384, T=30)
+        small = W.quad2d(3, K=512, T=30)
+    shape = dict(samples_per_cta=20, threads=256, positions_per_thread=npos)
     with gpu.Controller(small.params, tiling=shape) as g:
         g.set_obstacles(small.obstacles)
         assert g.kernel_regs() == 96
