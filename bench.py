@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -54,6 +55,29 @@ def kernel_src_sha():
         if f.endswith(".cuh") or (f.startswith("k_") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    architecture) and its logical CPU count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": name or platform.machine(), "logical_cpus": os.cpu_count()}
 
 
 def measured_peaks():
@@ -596,6 +620,10 @@ def main():
                 "ops_per_launch": algorithmic_ops(K, T, P, J)}
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved_tops / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    load_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if load_mhz:  # the pool's median SM clock under a power-capped GEMM load
+        roofline["frac_at_measured_load_clock"] = achieved_tops / (sms * 128 * load_mhz * 1e6 / 1e12)
+        roofline["measured_load_clock_mhz"] = load_mhz
 
     if rank != 0:
         return
@@ -615,9 +643,14 @@ def main():
         threads = os.cpu_count() or 1
         rate, steps, el, used = oracle_rate(world, min(K, args.ref_samples), args.cpu_seconds,
                                             threads=threads)
+        rate1, steps1, el1, _ = oracle_rate(world, min(K, args.ref_samples), args.cpu_seconds / 3,
+                                            threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
                                 "sample": f"full oracle step on {min(K, args.ref_samples)} of {K} "
-                                          f"samples (T={T}, J={J}, P={P}), {steps} steps in {el:.1f} s"}
+                                          f"samples (T={T}, J={J}, P={P}), {steps} steps in {el:.1f} s",
+                                "single_thread": {"value": rate1, "unit": UNIT,
+                                                  "sample": f"{steps1} steps in {el1:.1f} s"},
+                                "cpu": cpu_model()}
     print(json.dumps(line), flush=True)
 
 
