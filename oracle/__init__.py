@@ -28,6 +28,8 @@ _LIB = os.path.join(_HERE, "liborc_mppi.so")
 
 UNICYCLE = 0
 QUAD2D = 1
+ACKERMANN = 2
+QUAD5 = 3
 
 
 def build(force: bool = False) -> str:
@@ -60,6 +62,7 @@ class _Params(C.Structure):
         ("seed", C.c_uint64),
         ("mass", C.c_double), ("inertia", C.c_double),
         ("arm", C.c_double), ("gravity", C.c_double),
+        ("wheelbase", C.c_double),
     ]
 
 
@@ -127,7 +130,7 @@ def _f64(a, shape=None):
 
 
 def state_dim(model: int) -> int:
-    return 6 if model == QUAD2D else 3
+    return {QUAD2D: 6, ACKERMANN: 4, QUAD5: 5}.get(model, 3)
 
 
 def make_params(cfg: dict) -> _Params:

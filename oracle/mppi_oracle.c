@@ -38,6 +38,8 @@
 
 #define ORC_UNICYCLE 0
 #define ORC_QUAD2D 1
+#define ORC_ACKERMANN 2
+#define ORC_QUAD5 3
 #define ORC_MAXN 6
 #ifndef M_E
 #define M_E 2.7182818284590452354
@@ -48,7 +50,11 @@
 typedef struct {
   int32_t model; /* ORC_UNICYCLE: x=(x,y,theta), u=(v,omega);
                     ORC_QUAD2D:   x=(y,z,phi,ydot,zdot,phidot), u=(u1,u2) thrust
-                                  deviations, F_i = m g / 2 + u_i */
+                                  deviations, F_i = m g / 2 + u_i;
+                    ORC_ACKERMANN: x=(x,y,theta,v), u=(steering phi, accel a)
+                                  (Eq. 14);
+                    ORC_QUAD5:    x=(x,z,theta,vx,vz), u=(pitch rate omega,
+                                  thrust deviation u_t) (Eq. 12) */
   int32_t K, T;
   double dt, lambda;      /* lambda: temperature of Eq. 4 (divides the cost) */
   double sigma[4];        /* Sigma_u, 2x2 row-major, symmetric PSD */
@@ -66,6 +72,7 @@ typedef struct {
   double shape[16];       /* body-frame shape points (sx, sy) */
   uint64_t seed;
   double mass, inertia, arm, gravity; /* quadrotor constants */
+  double wheelbase;                   /* L of Eq. 14 */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -104,7 +111,14 @@ double orc_uniform(uint32_t r) {
   return (double)((r >> 8) | 1u) * (1.0 / 16777216.0);
 }
 
-static int state_dim(int model) { return model == ORC_QUAD2D ? 6 : 3; }
+static int state_dim(int model) {
+  switch (model) {
+    case ORC_QUAD2D: return 6;
+    case ORC_ACKERMANN: return 4;
+    case ORC_QUAD5: return 5;
+    default: return 3;
+  }
+}
 
 /* Lower Cholesky factor of a symmetric PSD 2x2 matrix A (row-major):
  * L = [[l00, 0], [l10, l11]], A = L L^T. */
@@ -161,6 +175,22 @@ void orc_dynamics(const orc_params* p, const double* x, const double* v,
     xn[0] = x[0] + v[0] * cos(x[2]) * dt;
     xn[1] = x[1] + v[0] * sin(x[2]) * dt;
     xn[2] = x[2] + v[1] * dt;
+  } else if (p->model == ORC_ACKERMANN) {
+    /* Eq. 14: position along the heading at speed v_k, heading rate
+     * v_k tan(phi) / L, speed rate a */
+    xn[0] = x[0] + x[3] * cos(x[2]) * dt;
+    xn[1] = x[1] + x[3] * sin(x[2]) * dt;
+    xn[2] = x[2] + x[3] * tan(v[0]) / p->wheelbase * dt;
+    xn[3] = x[3] + v[1] * dt;
+  } else if (p->model == ORC_QUAD5) {
+    /* Eq. 12, read with z in the second and fifth rows (the printed rows
+     * say y and v_y): pitch rate omega, thrust m g + u_t */
+    const double acc = (p->mass * p->gravity + v[1]) / p->mass;
+    xn[0] = x[0] + x[3] * dt;
+    xn[1] = x[1] + x[4] * dt;
+    xn[2] = x[2] + v[0] * dt;
+    xn[3] = x[3] - acc * sin(x[2]) * dt;
+    xn[4] = x[4] + (acc * cos(x[2]) - p->gravity) * dt;
   } else {
     double F1 = 0.5 * p->mass * p->gravity + v[0];
     double F2 = 0.5 * p->mass * p->gravity + v[1];

@@ -32,6 +32,8 @@ import numpy as np
 
 UNICYCLE = 0
 QUAD2D = 1
+ACKERMANN = 2
+QUAD5 = 3
 
 # Planar quadrotor constants printed in Sec. V-A (frame 0.4 m, mass 0.5 kg,
 # inertia 0.005 kg m^2, g = 9.81 m/s^2, thrust limit 0.981 N).
@@ -40,6 +42,10 @@ QUAD_INERTIA = 0.005
 QUAD_FRAME = 0.4
 GRAVITY = 9.81
 QUAD_THRUST_LIMIT = 0.981
+QUAD5_PITCH_RATE_LIMIT = 4.0  # rad/s (Sec. V-A)
+CAR_LENGTH, CAR_WIDTH = 4.0, 3.0  # footprint rectangle (Sec. V-B)
+CAR_WHEELBASE = 2.5  # not printed in the paper: a reading
+CAR_STEER_LIMIT, CAR_ACCEL_LIMIT = 1.013, 2.0  # rad, m/s^2 (Sec. V-B)
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -47,7 +53,7 @@ def rng(seed: int) -> np.random.Generator:
 
 
 def state_dim(model: int) -> int:
-    return 6 if model == QUAD2D else 3
+    return {QUAD2D: 6, ACKERMANN: 4, QUAD5: 5}.get(model, 3)
 
 
 def quad_shape_points() -> np.ndarray:
@@ -55,6 +61,14 @@ def quad_shape_points() -> np.ndarray:
     the two propellers, the centre and the quarter points between them."""
     s = np.arange(-3, 4) * (QUAD_FRAME / 6.0)
     return np.stack([s, np.zeros_like(s)], axis=1)
+
+
+def car_shape_points() -> np.ndarray:
+    """Eight points of the 4 m x 3 m rectangle around the vehicle position:
+    its corners and the midpoints of its sides (length along the heading)."""
+    a, b = CAR_LENGTH / 2.0, CAR_WIDTH / 2.0
+    return np.array([[a, b], [0.0, b], [-a, b], [-a, 0.0],
+                     [-a, -b], [0.0, -b], [a, -b], [a, 0.0]])
 
 
 def obstacle_field(g: np.random.Generator, J: int, lo, hi, r_lo: float,
@@ -89,6 +103,18 @@ def base_params(model: int, K: int, T: int, dt: float, seed: int) -> dict:
         p.update(sigma=[0.5, 0.0, 0.0, 0.5], Q=[1.0, 1.0, 0.0],
                  Qf=[10.0, 10.0, 0.0], u_min=[-1.0, -2.0], u_max=[2.0, 2.0],
                  shape=np.zeros((1, 2)))
+    elif model == ACKERMANN:  # Sec. V-B: Sigma_u, steering and acceleration limits
+        p.update(sigma=[0.075, 0.0, 0.0, 2.0], Q=[1.0, 1.0, 0.0, 0.1],
+                 Qf=[10.0, 10.0, 0.0, 1.0],
+                 u_min=[-CAR_STEER_LIMIT, -CAR_ACCEL_LIMIT],
+                 u_max=[CAR_STEER_LIMIT, CAR_ACCEL_LIMIT],
+                 shape=car_shape_points(), wheelbase=CAR_WHEELBASE)
+    elif model == QUAD5:  # Sec. V-A: Sigma_u, pitch-rate and thrust limits
+        p.update(sigma=[0.4, 0.0, 0.0, 0.12], Q=[1.0, 1.0, 0.1, 0.1, 0.1],
+                 Qf=[10.0, 10.0, 1.0, 1.0, 1.0],
+                 u_min=[-QUAD5_PITCH_RATE_LIMIT, -QUAD_THRUST_LIMIT],
+                 u_max=[QUAD5_PITCH_RATE_LIMIT, QUAD_THRUST_LIMIT],
+                 shape=quad_shape_points())
     else:
         p.update(sigma=[0.25, 0.0, 0.0, 0.25],
                  Q=[1.0, 1.0, 0.1, 0.1, 0.1, 0.1],
@@ -135,7 +161,10 @@ def line_reference(params: dict, start, goal, x, v_ref: float) -> np.ndarray:
     moving = (s < L).astype(np.float64)
     if model == UNICYCLE:
         ref[:, 2] = math.atan2(d[1], d[0])
-    else:
+    elif model == ACKERMANN:
+        ref[:, 2] = math.atan2(d[1], d[0])
+        ref[:, 3] = v_ref * moving
+    else:  # both quadrotors: velocities in dims 3 and 4
         ref[:, 3] = v_ref * d[0] * moving
         ref[:, 4] = v_ref * d[1] * moving
     return ref
@@ -144,7 +173,7 @@ def line_reference(params: dict, start, goal, x, v_ref: float) -> np.ndarray:
 def _goal_state(model: int, xy, heading: float = 0.0) -> np.ndarray:
     g = np.zeros(state_dim(model))
     g[0], g[1] = xy
-    if model == UNICYCLE:
+    if model in (UNICYCLE, ACKERMANN):
         g[2] = heading
     return g
 
@@ -223,8 +252,46 @@ def serving_mix(n: int = 1000, seed: int = 0) -> list[World]:
     return [_mixed_world(g, i, seed, 512, 32768, 20, 100, 5, 500) for i in range(n)]
 
 
+def ackermann(seed: int = 0, K: int = 1024, T: int = 20, J: int = 5) -> World:
+    """The ground-vehicle mission of Sec. V-B in synthetic form: K = M = 1024
+    samples, T = N = 20 steps of 0.02 s, J circles of radius 4.3 m along a
+    100 m x 30 m corridor, alternately above and below the centre line so
+    that the vehicle (4 m x 3 m, 8 shape points) passes narrow gaps, at a
+    reference speed of 5 m/s.  The paper publishes no layout."""
+    g = rng(seed)
+    p = base_params(ACKERMANN, K=K, T=T, dt=0.02, seed=seed)
+    start = np.array([5.0, 15.0, 0.0, 0.0])
+    goal = _goal_state(ACKERMANN, (95.0, 15.0), 0.0)
+    xs = np.sort(g.uniform(20.0, 80.0, J))
+    side = np.where(np.arange(J) % 2 == 0, 1.0, -1.0)
+    ys = 15.0 + side * g.uniform(5.5, 7.0, J)  # gaps of about 1.2 to 2.7 m each side
+    obs = np.stack([xs, ys, np.full(J, 4.3)], axis=1)
+    p["x_goal"] = goal
+    return World(p, obs, start, goal, v_ref=5.0, name="ackermann")
+
+
+def quad5(seed: int = 0, K: int = 1024, T: int = 20, J: int = 3) -> World:
+    """The quadrotor mission of Sec. V-A with the paper's 5-state model, in
+    synthetic form: K = 1024, T = 20 steps of 0.02 s, J circles of radius
+    0.8 m along a 20 m x 10 m corridor, alternately above and below the
+    flight line, hover start, reference speed 1 m/s."""
+    g = rng(seed)
+    p = base_params(QUAD5, K=K, T=T, dt=0.02, seed=seed)
+    start = np.zeros(5)
+    start[:2] = (1.0, 5.0)
+    goal = _goal_state(QUAD5, (19.0, 5.0))
+    xs = np.sort(g.uniform(5.0, 15.0, J))
+    side = np.where(np.arange(J) % 2 == 0, 1.0, -1.0)
+    zs = 5.0 + side * g.uniform(1.2, 1.6, J)
+    obs = np.stack([xs, zs, np.full(J, 0.8)], axis=1)
+    p["x_goal"] = goal
+    return World(p, obs, start, goal, v_ref=1.0, name="quad5")
+
+
 PRESETS = {
     "unicycle_small": unicycle_small,
     "quad2d": quad2d,
     "unicycle_stress": unicycle_stress,
+    "ackermann": ackermann,
+    "quad5": quad5,
 }

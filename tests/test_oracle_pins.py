@@ -225,6 +225,85 @@ def test_quad_closed_forms(orc):
         assert X[k, 0] == pytest.approx(-g * math.sin(phi) * dt**2 * k * (k - 1) / 2, abs=1e-12)
 
 
+def _car_cfg(**over):
+    p = W.base_params(W.ACKERMANN, K=4, T=5, dt=0.02, seed=3)
+    p.update(x_goal=np.zeros(4))
+    p.update(over)
+    return p
+
+
+def test_ackermann_straight_constant_acceleration(orc):
+    """Eq. 14 with zero steering: the heading stays, v_k = v0 + k a dt and
+    x_k = x0 + cos(th0) dt sum_{j<k} v_j = x0 + cos(th0) dt (k v0 + a dt k(k-1)/2)."""
+    dt, a = 0.02, 1.5
+    p = _car_cfg(dt=dt)
+    x0 = np.array([3.0, -2.0, 0.6, 2.0])
+    X = orc.simulate(p, x0, np.tile([0.0, a], (30, 1)))
+    for k in range(31):
+        s = k * x0[3] + a * dt * k * (k - 1) / 2
+        np.testing.assert_allclose(X[k], [x0[0] + math.cos(x0[2]) * dt * s,
+                                          x0[1] + math.sin(x0[2]) * dt * s,
+                                          x0[2], x0[3] + k * a * dt], rtol=0, atol=1e-12)
+
+
+def test_ackermann_constant_steering_closed_form(orc):
+    """Eq. 14 at constant speed and steering: heading rate w = v tan(phi) / L,
+    so the position is the unicycle's Dirichlet sum with (v, w)."""
+    dt, v, phi, L = 0.02, 4.0, 0.3, W.CAR_WHEELBASE
+    p = _car_cfg(dt=dt)
+    x0 = np.array([1.0, 2.0, -0.4, v])
+    X = orc.simulate(p, x0, np.tile([phi, 0.0], (40, 1)))
+    a = v * math.tan(phi) / L * dt
+    for k in range(41):
+        if k == 0:
+            sx = sy = 0.0
+        else:
+            D = math.sin(k * a / 2) / math.sin(a / 2)
+            sx = D * math.cos(x0[2] + (k - 1) * a / 2)
+            sy = D * math.sin(x0[2] + (k - 1) * a / 2)
+        np.testing.assert_allclose(X[k], [x0[0] + v * dt * sx, x0[1] + v * dt * sy,
+                                          x0[2] + k * a, v], rtol=0, atol=1e-11)
+
+
+def _quad5_cfg(**over):
+    p = W.base_params(W.QUAD5, K=4, T=5, dt=0.02, seed=3)
+    p.update(x_goal=np.zeros(5))
+    p.update(over)
+    return p
+
+
+def test_quad5_hover_is_fixed_point(orc):
+    """Eq. 12: level attitude, zero pitch rate and zero thrust deviation
+    (thrust m g) leave the state unchanged."""
+    p = _quad5_cfg()
+    x0 = np.array([1.0, 5.0, 0.0, 0.0, 0.0])
+    X = orc.simulate(p, x0, np.zeros((30, 2)))
+    np.testing.assert_allclose(X, np.tile(x0, (31, 1)), atol=1e-15)
+
+
+def test_quad5_closed_forms(orc):
+    m, g, dt = W.QUAD_MASS, W.GRAVITY, 0.02
+    p = _quad5_cfg()
+    # level, extra thrust u: vertical acceleration u / m, horizontal drift
+    u = 0.4
+    x0 = np.array([0.5, 2.0, 0.0, 0.3, -0.2])
+    X = orc.simulate(p, x0, np.tile([0.0, u], (25, 1)))
+    for k in range(26):
+        assert X[k, 0] == pytest.approx(x0[0] + k * x0[3] * dt, abs=1e-12)
+        assert X[k, 1] == pytest.approx(x0[1] + k * x0[4] * dt + (u / m) * dt**2 * k * (k - 1) / 2,
+                                        abs=1e-12)
+        assert X[k, 4] == pytest.approx(x0[4] + k * (u / m) * dt, abs=1e-12)
+    # constant pitch rate, hover thrust: theta_k = k w dt, and the
+    # horizontal velocity sums -g sin(theta_j) dt over j < k (Dirichlet form)
+    w = 1.5
+    X = orc.simulate(p, np.zeros(5), np.tile([w, 0.0], (20, 1)))
+    a = w * dt
+    for k in range(21):
+        assert X[k, 2] == pytest.approx(k * a, abs=1e-12)
+        sv = 0.0 if k == 0 else math.sin(k * a / 2) / math.sin(a / 2) * math.sin((k - 1) * a / 2)
+        assert X[k, 3] == pytest.approx(-g * dt * sv, abs=1e-11)
+
+
 # ---------------------------------------------------------------- barrier (Eq. 5, Eq. 13/15)
 
 def test_bsum_single_pair_and_floor(orc):
@@ -413,15 +492,13 @@ def test_weights_brute_force_small(orc):
         np.testing.assert_allclose(w, bf, rtol=1e-13)
 
 
-@pytest.mark.parametrize("model", [W.UNICYCLE, W.QUAD2D])
+@pytest.mark.parametrize("model", [W.UNICYCLE, W.QUAD2D, W.ACKERMANN, W.QUAD5])
 def test_step_update_brute_force(orc, model):
     """Full iteration at K <= 8: du_eff must be clamp(U + NLN draw) - U for the
     same counter, and U* = clamp(U + sum_k w_k du_eff_k) recomputed with
     explicit loops and the brute-force weights; then the shift."""
-    if model == W.UNICYCLE:
-        w = W.unicycle_small(3)
-    else:
-        w = W.quad2d(3)
+    w = {W.UNICYCLE: W.unicycle_small, W.QUAD2D: W.quad2d, W.ACKERMANN: W.ackermann,
+         W.QUAD5: W.quad5}[model](3)
     p = dict(w.params)
     p.update(K=8, T=6)
     g = np.random.default_rng(8)
