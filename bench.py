@@ -212,7 +212,8 @@ def describe(world):
     P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
     return {"workload": world.name, "K": int(p["K"]), "T": int(p["T"]),
             "obstacles": int(world.obstacles.shape[0]), "shape_points": P,
-            "model": "planar quadrotor" if p["model"] == 1 else "unicycle",
+            "model": {0: "unicycle", 1: "planar quadrotor (6 states)", 2: "Ackermann vehicle",
+                      3: "planar quadrotor (5 states, the paper's)"}[int(p["model"])],
             "l2": "flushed between timed steps (256 MB write)"}
 
 

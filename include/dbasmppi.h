@@ -41,14 +41,22 @@ extern "C" {
 #define MPPI_ETIMEOUT (-4) /* a bounded device-side wait expired */
 #define MPPI_ESTATE (-5)   /* call out of order (e.g. no step yet) */
 
-/* Dynamics (Eq. 1).  MPPI_UNICYCLE: state (x, y, theta), control (v, omega),
- * x' = x + v cos(theta) dt, y' = y + v sin(theta) dt, theta' = theta + omega dt.
- * MPPI_QUAD2D: planar quadrotor with the constants of Sec. V-A, state
- * (y, z, phi, ydot, zdot, phidot), control (u1, u2) = thrust deviations with
- * F_i = m g / 2 + u_i; explicit Euler with the right-hand side at step k as
- * in Eq. 12. */
+/* Dynamics (Eq. 1), explicit Euler with the right-hand side at step k as
+ * in Eq. 12 and Eq. 14.  MPPI_UNICYCLE: state (x, y, theta), control
+ * (v, omega), x' = x + v cos(theta) dt, y' = y + v sin(theta) dt,
+ * theta' = theta + omega dt.  MPPI_QUAD2D: planar quadrotor with the
+ * constants of Sec. V-A, state (y, z, phi, ydot, zdot, phidot), control
+ * (u1, u2) = thrust deviations with F_i = m g / 2 + u_i.  MPPI_ACKERMANN: the
+ * ground vehicle of Eq. 14, state (x, y, theta, v), control (steering phi,
+ * acceleration a), theta' = theta + v tan(phi) / wheelbase dt, v' = v + a dt.
+ * MPPI_QUAD5: the planar quadrotor of Eq. 12, state (x, z, theta, vx, vz),
+ * control (pitch rate omega, thrust deviation u_t), thrust m g + u_t.  The
+ * shape points of every model sit at (state[0], state[1]) + R(state[2]) s. */
 #define MPPI_UNICYCLE 0
 #define MPPI_QUAD2D 1
+#define MPPI_ACKERMANN 2
+#define MPPI_QUAD5 3
+#define MPPI_NUM_MODELS 4
 
 /* Size limits. */
 #define MPPI_MAX_T 256        /* horizon */
@@ -71,8 +79,9 @@ extern "C" {
  * [u_min, u_max] is G(u) <= 0 of Eq. 2 and is applied by clamping.  x_goal is
  * x_d of Eq. 7.  shape holds n_shape body-frame points (sx, sy), placed at
  * position + R(heading) (sx, sy).  seed keys the Philox4x32-10 generator.
- * mass, inertia, arm, gravity are the quadrotor constants (unused by the
- * unicycle). */
+ * mass, inertia, arm, gravity are the quadrotor constants (mass and gravity
+ * also for MPPI_QUAD5); wheelbase is L of Eq. 14 (MPPI_ACKERMANN, > 0, whose
+ * steering limits must lie inside (-pi/2, pi/2)). */
 typedef struct mppi_params {
   int32_t model;
   int32_t K, T;
@@ -89,6 +98,7 @@ typedef struct mppi_params {
   double shape[2 * MPPI_MAX_SHAPE];
   uint64_t seed;
   double mass, inertia, arm, gravity;
+  double wheelbase;
 } mppi_params;
 
 /* Kernel launch shape.  Zero fields are chosen by the library. */
@@ -294,12 +304,12 @@ int mppi_batch_set_graph(mppi_batch* b, int32_t enable);
 
 /* Tiling policy of a batch: the launch shape given to controllers that
  * mppi_batch_add receives without an explicit tiling, per model (index
- * MPPI_UNICYCLE, MPPI_QUAD2D).  samples_per_cta in 1..32 (capped at K);
+ * MPPI_UNICYCLE .. MPPI_QUAD5).  samples_per_cta in 1..32 (capped at K);
  * positions_per_thread 8 or 14, or 0 to choose from n_shape.  The batch
  * kernel's CTAs have 256 threads.  Default: {32, 32}, {0, 0}. */
 typedef struct {
-  int32_t samples_per_cta[2];
-  int32_t positions_per_thread[2];
+  int32_t samples_per_cta[MPPI_NUM_MODELS];
+  int32_t positions_per_thread[MPPI_NUM_MODELS];
 } mppi_batch_policy;
 
 /* Set or read the policy used by later mppi_batch_add calls (controllers
@@ -310,7 +320,8 @@ int mppi_batch_get_policy(const mppi_batch* b, mppi_batch_policy* pol);
 /* Autotuner of the batched step.  For n representative controllers
  * (parameters ps[i], obstacles cxcyrs[i] with Js[i] rows), each model's
  * policy in turn is chosen from samples_per_cta {8, 16, 32} x
- * positions_per_thread {8, 14} (the other model's held at its best so far):
+ * positions_per_thread {8, 14} (the other models' held at their best so far;
+ * models absent from the set are skipped):
  * for each candidate a temporary batch of pool_bytes holds all n
  * controllers, and `iters` graph-replayed steps of all of them (each from
  * its x_goal) are timed with CUDA events after two untimed ones.  best

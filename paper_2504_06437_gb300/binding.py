@@ -15,8 +15,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _LIB = os.path.join(_HERE, "libdbasmppi.so")
-_SOURCES = ["csrc/dbasmppi.cu", "csrc/k_step_u.cu", "csrc/k_step_q.cu", "csrc/k_step_u_r80.cu",
-            "csrc/k_step_q_r80.cu", "csrc/k_batch.cu"]
+_SOURCES = ["csrc/dbasmppi.cu", "csrc/k_step_u.cu", "csrc/k_step_q.cu", "csrc/k_step_a.cu",
+            "csrc/k_step_p.cu", "csrc/k_step_u_r80.cu", "csrc/k_step_q_r80.cu",
+            "csrc/k_step_a_r80.cu", "csrc/k_step_p_r80.cu", "csrc/k_batch.cu",
+            "csrc/k_batch_all.cu"]
 _DEPS = _SOURCES + ["csrc/mppi_device.cuh", "csrc/mppi_tile.cuh", "csrc/kernels.cuh"]
 HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
 
@@ -24,7 +26,12 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread"]
 
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE = 0, -1, -2, -3, -4, -5
-UNICYCLE, QUAD2D = 0, 1
+UNICYCLE, QUAD2D, ACKERMANN, QUAD5 = 0, 1, 2, 3
+NUM_MODELS = 4
+
+
+def state_dim(model: int) -> int:
+    return {QUAD2D: 6, ACKERMANN: 4, QUAD5: 5}.get(int(model), 3)
 MAX_SHAPE = 8
 
 
@@ -88,6 +95,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("mass", C.c_double), ("inertia", C.c_double),
         ("arm", C.c_double), ("gravity", C.c_double),
+        ("wheelbase", C.c_double),
     ]
 
 
@@ -97,7 +105,8 @@ class Tiling(C.Structure):
 
 
 class BatchPolicy(C.Structure):
-    _fields_ = [("samples_per_cta", C.c_int32 * 2), ("positions_per_thread", C.c_int32 * 2)]
+    _fields_ = [("samples_per_cta", C.c_int32 * NUM_MODELS),
+                ("positions_per_thread", C.c_int32 * NUM_MODELS)]
 
 
 _lib = None
@@ -235,7 +244,7 @@ class Controller:
         self.cfg = dict(cfg)
         self.params = make_params(cfg)
         self.K, self.T = int(self.params.K), int(self.params.T)
-        self.n = 6 if self.params.model == QUAD2D else 3
+        self.n = state_dim(self.params.model)
         h = C.c_void_p()
         u = None if u_init is None else _f64(u_init).reshape(self.T, 2)
         self._u_init = u
@@ -376,7 +385,7 @@ class Batch:
         _check(load().mppi_batch_add(self.h, C.byref(p), _ptr(u) if u is not None else None,
                                      C.byref(t) if t is not None else None,
                                      _ptr(ob) if ob.size else None, ob.shape[0], C.byref(slot)))
-        self.info[slot.value] = (T, 6 if p.model == QUAD2D else 3, int(p.K))
+        self.info[slot.value] = (T, state_dim(p.model), int(p.K))
         return slot.value
 
     def set_obstacles(self, slot: int, obstacles):
@@ -448,16 +457,19 @@ class Batch:
 
 
 def _policy(d: dict) -> BatchPolicy:
+    """Per-model lists; models past the end of a shorter list take the
+    library's defaults (32 samples per CTA, points per thread chosen)."""
     pol = BatchPolicy()
-    for m in range(2):
-        pol.samples_per_cta[m] = int(d["samples_per_cta"][m])
-        pol.positions_per_thread[m] = int(d["positions_per_thread"][m])
+    S, NP = list(d["samples_per_cta"]), list(d["positions_per_thread"])
+    for m in range(NUM_MODELS):
+        pol.samples_per_cta[m] = int(S[m]) if m < len(S) else 32
+        pol.positions_per_thread[m] = int(NP[m]) if m < len(NP) else 0
     return pol
 
 
 def _policy_dict(pol: BatchPolicy) -> dict:
-    return dict(samples_per_cta=[pol.samples_per_cta[0], pol.samples_per_cta[1]],
-                positions_per_thread=[pol.positions_per_thread[0], pol.positions_per_thread[1]])
+    return dict(samples_per_cta=[pol.samples_per_cta[m] for m in range(NUM_MODELS)],
+                positions_per_thread=[pol.positions_per_thread[m] for m in range(NUM_MODELS)])
 
 
 def batch_autotune(cfgs, obstacles, iters: int = 3, pool_bytes: int = 2 << 30):
@@ -517,7 +529,7 @@ class Server:
         if rc == MPPI_ENOMEM:
             return None
         _check(rc)
-        self.dims[r.value] = (int(p.T), 6 if p.model == QUAD2D else 3)
+        self.dims[r.value] = (int(p.T), state_dim(p.model))
         return r.value
 
     def leave(self, robot: int):

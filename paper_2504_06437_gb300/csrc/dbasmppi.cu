@@ -79,9 +79,13 @@ __global__ void draws_kernel(int K, int T, uint32_t k0, uint32_t k1, uint32_t it
 using StepFn = void (*)(CtrlDesc, const double*, const double*);
 
 StepFn pick_kernel(int model, int npos, bool r80) {
-  if (model == MPPI_UNICYCLE)
-    return npos == 14 ? (r80 ? step_u14_r80 : step_u14) : (r80 ? step_u8_r80 : step_u8);
-  return npos == 14 ? (r80 ? step_q14_r80 : step_q14) : (r80 ? step_q8_r80 : step_q8);
+  // [model][points 8 / 14][register form 96 / 80]
+  static const StepFn table[MPPI_NUM_MODELS][2][2] = {
+      {{step_u8, step_u8_r80}, {step_u14, step_u14_r80}},
+      {{step_q8, step_q8_r80}, {step_q14, step_q14_r80}},
+      {{step_a8, step_a8_r80}, {step_a14, step_a14_r80}},
+      {{step_p8, step_p8_r80}, {step_p14, step_p14_r80}}};
+  return table[model][npos == 14 ? 1 : 0][r80 ? 1 : 0];
 }
 
 // World points a barrier thread holds: whole units of P points each; the
@@ -101,7 +105,14 @@ int pick_npos(int P) {
   return best;
 }
 
-int state_dim(int model) { return model == MPPI_QUAD2D ? 6 : 3; }
+int state_dim(int model) {
+  switch (model) {
+    case MPPI_QUAD2D: return 6;
+    case MPPI_ACKERMANN: return 4;
+    case MPPI_QUAD5: return 5;
+    default: return 3;
+  }
+}
 
 bool finite_all(const double* a, int n) {
   for (int i = 0; i < n; ++i)
@@ -121,7 +132,7 @@ int check_obstacle(const double* o, int j) {
 
 int validate(const mppi_params* p) {
   if (!p) return fail(MPPI_EINVAL, "params is NULL");
-  if (p->model != MPPI_UNICYCLE && p->model != MPPI_QUAD2D)
+  if (p->model < 0 || p->model >= MPPI_NUM_MODELS)
     return fail(MPPI_EINVAL, "unknown model %d", p->model);
   if (p->K < 1 || p->K > MPPI_MAX_K) return fail(MPPI_EINVAL, "K=%d out of [1, %d]", p->K, MPPI_MAX_K);
   if (p->T < 1 || p->T > MPPI_MAX_T) return fail(MPPI_EINVAL, "T=%d out of [1, %d]", p->T, MPPI_MAX_T);
@@ -129,8 +140,8 @@ int validate(const mppi_params* p) {
     return fail(MPPI_EINVAL, "n_shape=%d out of [1, %d]", p->n_shape, MPPI_MAX_SHAPE);
   const double sc[] = {p->dt,      p->lambda,     p->ln_mu, p->ln_sigma, p->mu_coarse,
                        p->gamma_ctrl, p->gamma_bas, p->R_B,   p->C_coll,   p->h_eps,
-                       p->mass,    p->inertia,    p->arm,   p->gravity};
-  if (!finite_all(sc, 14) || !finite_all(p->sigma, 4) || !finite_all(p->Q, 6) ||
+                       p->mass,    p->inertia,    p->arm,   p->gravity, p->wheelbase};
+  if (!finite_all(sc, 15) || !finite_all(p->sigma, 4) || !finite_all(p->Q, 6) ||
       !finite_all(p->Qf, 6) || !finite_all(p->u_min, 2) || !finite_all(p->u_max, 2) ||
       !finite_all(p->x_goal, 6) || !finite_all(p->shape, 2 * p->n_shape))
     return fail(MPPI_EINVAL, "non-finite parameter");
@@ -149,6 +160,14 @@ int validate(const mppi_params* p) {
     return fail(MPPI_EINVAL, "Sigma must be positive definite when gamma_ctrl != 0");
   if (p->model == MPPI_QUAD2D && !(p->mass > 0 && p->inertia > 0))
     return fail(MPPI_EINVAL, "quadrotor mass and inertia must be > 0");
+  if (p->model == MPPI_QUAD5 && !(p->mass > 0))
+    return fail(MPPI_EINVAL, "quadrotor mass must be > 0");
+  if (p->model == MPPI_ACKERMANN) {
+    if (!(p->wheelbase > 0)) return fail(MPPI_EINVAL, "wheelbase must be > 0");
+    // tan(steering) of Eq. 14 is finite only inside (-pi/2, pi/2)
+    if (!(p->u_min[0] > -1.5707963267948966 && p->u_max[0] < 1.5707963267948966))
+      return fail(MPPI_EINVAL, "steering limits must lie inside (-pi/2, pi/2)");
+  }
   return MPPI_OK;
 }
 
@@ -208,9 +227,11 @@ int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, S
   std::lock_guard<std::mutex> lock(g_pick_mu);
   if (!g_step_attr[dev]) {
     const int lim = max_smem_optin();
-    const StepFn fns[8] = {step_u8,     step_u14,     step_q8,     step_q14,
-                           step_u8_r80, step_u14_r80, step_q8_r80, step_q14_r80};
-    for (StepFn f : fns) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    for (int m = 0; m < MPPI_NUM_MODELS; ++m)
+      for (int np : {8, 14})
+        for (bool r80 : {false, true})
+          CK(cudaFuncSetAttribute(pick_kernel(m, np, r80),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     g_step_attr[dev] = true;
   }
   PickMemo& m = g_pick_memo[dev];
@@ -393,8 +414,10 @@ void fill_desc(mppi_ctx* c) {
   for (int i = 0; i < 2 * kMaxShape; ++i)
     D.shape[i] = i < 2 * p->n_shape ? (float)p->shape[i] : 0.0f;
   D.g = (float)p->gravity;
-  D.inv_mass = p->model == MPPI_QUAD2D ? (float)(1.0 / p->mass) : 0.0f;
-  D.arm_over_I = p->model == MPPI_QUAD2D ? (float)(p->arm / p->inertia) : 0.0f;
+  D.inv_mass = (p->model == MPPI_QUAD2D || p->model == MPPI_QUAD5) ? (float)(1.0 / p->mass) : 0.0f;
+  D.k_turn = p->model == MPPI_QUAD2D      ? (float)(p->arm / p->inertia)
+             : p->model == MPPI_ACKERMANN ? (float)(1.0 / p->wheelbase)
+                                          : 0.0f;
   D.lambda = p->lambda;
   D.inv_lambda = 1.0 / p->lambda;
   D.inv_lambda_f = (float)(1.0 / p->lambda);
@@ -701,8 +724,7 @@ int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas) {
 int mppi_get_kernel_regs(mppi_ctx* c, int32_t* regs_cap) {
   if (!c) return fail(MPPI_ESTATE, "context is NULL");
   if (!regs_cap) return fail(MPPI_EINVAL, "regs_cap is NULL");
-  const bool r80 = c->fn == step_u8_r80 || c->fn == step_u14_r80 || c->fn == step_q8_r80 ||
-                   c->fn == step_q14_r80;
+  const bool r80 = c->fn == pick_kernel(c->p.model, c->tl.positions_per_thread, true);
   *regs_cap = r80 ? DBM_STEP_MAXNREG_R80 : DBM_STEP_MAXNREG;
   return MPPI_OK;
 }
@@ -1082,7 +1104,7 @@ struct mppi_batch {
   cudaStream_t own = nullptr;
   int use_graph = 1;
   int max_smem = 0;
-  mppi_batch_policy pol = {{32, 32}, {0, 0}};
+  mppi_batch_policy pol = {{32, 32, 32, 32}, {0, 0, 0, 0}};
 };
 
 namespace {
@@ -1192,10 +1214,14 @@ int batch_max_smem(mppi_batch* b) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     size_t stat = 0;
-    if (cudaFuncGetAttributes(&fa, batch_kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, batch_kernel_all) == cudaSuccess) stat = fa.sharedSizeBytes;
+    else cudaGetLastError();
+    if (cudaFuncGetAttributes(&fa, batch_kernel) == cudaSuccess && fa.sharedSizeBytes > stat)
+      stat = fa.sharedSizeBytes;
     else cudaGetLastError();
     b->max_smem = v - align_up((int)stat + 64, 128);
     cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b->max_smem);
+    cudaFuncSetAttribute(batch_kernel_all, cudaFuncAttributeMaxDynamicSharedMemorySize, b->max_smem);
   }
   return b->max_smem;
 }
@@ -1473,8 +1499,13 @@ int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, cons
   hdr->n_items = (int)n_items;
   hdr->next = 0u;
   hdr->inputs_off = (int)inputs_off;
+  // batch_kernel covers the unicycle and the 6-state quadrotor; a step that
+  // holds the Ackermann vehicle or the 5-state quadrotor takes batch_kernel_all
+  bool all_models = false;
+  for (int i = 0; i < n; ++i) all_models = all_models || b->slots[slots[i]].p.model >= 2;
+  const auto kernel = all_models ? batch_kernel_all : batch_kernel;
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchThreads, smem));
   if (occ < 1) return fail(MPPI_EINVAL, "batch needs %d bytes of shared memory per CTA", smem);
   const int grid = (int)std::min<size_t>((size_t)num_sms() * occ, n_items);
   std::vector<int> key(slots, slots + n);
@@ -1486,7 +1517,7 @@ int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, cons
     drop_lane_graph(L);
     if (allow_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(L.d_stage, L.h_stage, bytes, cudaMemcpyHostToDevice, st);
-    batch_kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, L.d_stage, L.d_out);
+    kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, L.d_stage, L.d_out);
     cudaMemcpyAsync(L.h_out, L.d_out, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st);
     if (allow_graph) {
       CK(cudaStreamEndCapture(st, &L.graph));
@@ -1583,7 +1614,7 @@ int mppi_batch_set_graph(mppi_batch* b, int32_t enable) {
 int mppi_batch_set_policy(mppi_batch* b, const mppi_batch_policy* pol) {
   if (!b) return fail(MPPI_ESTATE, "batch is NULL");
   if (!pol) return fail(MPPI_EINVAL, "policy is NULL");
-  for (int m = 0; m < 2; ++m) {
+  for (int m = 0; m < MPPI_NUM_MODELS; ++m) {
     if (pol->samples_per_cta[m] < 1 || pol->samples_per_cta[m] > 32)
       return fail(MPPI_EINVAL, "samples_per_cta must be in 1..32");
     const int np = pol->positions_per_thread[m];
@@ -1660,14 +1691,14 @@ int mppi_batch_autotune(const mppi_params* ps, const double* const* cxcyrs, cons
     if (int rc = validate(&ps[i])) return rc;
     for (int d = 0; d < 6; ++d) x0s[(size_t)i * 6 + d] = ps[i].x_goal[d];
   }
-  mppi_batch_policy cur = {{32, 32}, {0, 0}};
+  mppi_batch_policy cur = {{32, 32, 32, 32}, {0, 0, 0, 0}};
   float cur_ms = 0.0f;
   int rc = 0;
   if (!time_policy(ps, cxcyrs, Js, n, iters, pool_bytes, cur, x0s, &cur_ms, &rc))
     return rc ? rc : fail(MPPI_ECUDA, "timing the default policy failed");
   const int S_opts[3] = {8, 16, 32};
   const int NP_opts[2] = {8, 14};
-  for (int m = 0; m < 2; ++m) {
+  for (int m = 0; m < MPPI_NUM_MODELS; ++m) {
     bool present = false;
     for (int i = 0; i < n; ++i) present = present || ps[i].model == m;
     if (!present) continue;

@@ -1,0 +1,18 @@
+// One-controller step kernels of the Ackermann vehicle (Eq. 14).
+#include "kernels.cuh"
+
+namespace dbm {
+
+__global__ void __maxnreg__(DBM_STEP_MAXNREG) step_a8(const __grid_constant__ CtrlDesc D,
+                                                     const double* __restrict__ x0,
+                                                     const double* __restrict__ xref) {
+  step_body<2, 8>(D, x0, xref);
+}
+
+__global__ void __maxnreg__(DBM_STEP_MAXNREG) step_a14(const __grid_constant__ CtrlDesc D,
+                                                      const double* __restrict__ x0,
+                                                      const double* __restrict__ xref) {
+  step_body<2, 14>(D, x0, xref);
+}
+
+}  // namespace dbm

@@ -24,8 +24,10 @@ namespace dbm {
 #define DBM_STEP_MAXNREG_R80 80
 #endif
 
-// One step of one controller: one CTA per tile (MODEL: 0 unicycle,
-// 1 planar quadrotor; 8 or 14 world points per barrier thread).
+// One step of one controller: one CTA per tile (MODEL: 0 unicycle (u),
+// 1 planar quadrotor with two thrusts (q), 2 Ackermann vehicle (a), 3 the
+// paper's 5-state planar quadrotor (p); 8 or 14 world points per barrier
+// thread).
 __global__ void step_u8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                         const double* __restrict__ xref);
 __global__ void step_u14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
@@ -34,6 +36,14 @@ __global__ void step_q8(const __grid_constant__ CtrlDesc D, const double* __rest
                         const double* __restrict__ xref);
 __global__ void step_q14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                          const double* __restrict__ xref);
+__global__ void step_a8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                        const double* __restrict__ xref);
+__global__ void step_a14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                         const double* __restrict__ xref);
+__global__ void step_p8(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                        const double* __restrict__ xref);
+__global__ void step_p14(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                         const double* __restrict__ xref);
 __global__ void step_u8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                             const double* __restrict__ xref);
 __global__ void step_u14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
@@ -41,6 +51,14 @@ __global__ void step_u14_r80(const __grid_constant__ CtrlDesc D, const double* _
 __global__ void step_q8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                             const double* __restrict__ xref);
 __global__ void step_q14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_a8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                            const double* __restrict__ xref);
+__global__ void step_a14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_p8_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                            const double* __restrict__ xref);
+__global__ void step_p14_r80(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                              const double* __restrict__ xref);
 
 // Batched step: persistent CTAs pull (controller, tile) work items.
@@ -62,6 +80,9 @@ struct BatchHdr {
 constexpr int kBatchThreads = 256;
 __global__ void batch_kernel(const CtrlDesc* __restrict__ descs, unsigned char* stage,
                              double* __restrict__ u0_out);
+// The same over all four models (launched when a step holds model 2 or 3).
+__global__ void batch_kernel_all(const CtrlDesc* __restrict__ descs, unsigned char* stage,
+                                 double* __restrict__ u0_out);
 
 // Body of the one-controller step kernels.
 template <int MODEL, int NPOS>

@@ -93,7 +93,9 @@ struct CtrlDesc {
   float umin[2], umax[2];
   float Q[kMaxN], Qf[kMaxN];
   float shape[2 * kMaxShape];
-  float g, inv_mass, arm_over_I, inv_lambda_f;
+  float g, inv_mass;
+  float k_turn;              // arm / I (6-state quadrotor) or 1 / wheelbase (Ackermann)
+  float inv_lambda_f;
   double lambda, inv_lambda, mu_coarse, gamma_ctrl, gamma_bas, R_B_d;
   double umin_d[2], umax_d[2];
   int nscl;
@@ -390,9 +392,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int ma
 // ------------------------------------------------------------------ dynamics
 // State dimension of each model (the Euler steps themselves are evaluated in
 // scan form, see scan_trajectory).
+// Models: 0 unicycle, 1 planar quadrotor (6 states, two thrusts), 2 Ackermann
+// vehicle (Eq. 14), 3 the paper's planar quadrotor (5 states, Eq. 12).
 template <int MODEL>
 struct Dyn {
-  static constexpr int n = MODEL == 0 ? 3 : 6;
+  static constexpr int n = MODEL == 0 ? 3 : MODEL == 1 ? 6 : MODEL == 2 ? 4 : 5;
 };
 
 // ------------------------------------------------------------ tile kernel body

@@ -80,13 +80,16 @@ __device__ inline void prep_constants(const CtrlDesc& D, const double* Usrc, con
   __syncthreads();
 }
 
-// One trajectory of T explicit-Euler steps (Eq. 1, 12) under the controls
-// V[t * vs], from the initial state x_init (position rebased to the origin),
-// evaluated by the 32 lanes of one warp: lanes take steps t = t0 + lane in
-// segments of 32, and every state component is a prefix sum over steps of
-// increments that depend only on components earlier in the chain
-//   unicycle:  theta -> (cos, sin) -> (x, y)
-//   quadrotor: phidot -> phi -> (cos, sin) -> (ydot, zdot) -> (y, z)
+// One trajectory of T explicit-Euler steps (Eq. 1, 12, 14) under the
+// controls V[t * vs], from the initial state x_init (position rebased to the
+// origin), evaluated by the 32 lanes of one warp: lanes take steps
+// t = t0 + lane in segments of 32, and every state component is a prefix sum
+// over steps of increments that depend only on components earlier in the
+// chain
+//   unicycle:          theta -> (cos, sin) -> (x, y)
+//   quadrotor (6):     phidot -> phi -> (cos, sin) -> (ydot, zdot) -> (y, z)
+//   Ackermann:         v -> theta -> (cos, sin) -> (x, y)
+//   quadrotor (5):     theta -> (cos, sin) -> (vx, vz) -> (x, z)
 // so each segment is a few warp scans, carried from segment to segment.  The
 // pose after step t is written to pose[t * ps] as (x, y, cos, sin) of the
 // heading.  With COST the lane also adds to `cost` its steps' stage cost
@@ -143,12 +146,135 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
       cy = lane31(ya);
     }
     if constexpr (COST) ff_add(cost, lc);
+  } else if constexpr (MODEL == 2) {
+    // Ackermann (Eq. 14): speed -> heading (rate v tan(steer) / L) ->
+    // (cos, sin) -> position, each a prefix sum over the segment's steps
+    float cx = x_init[0], cy = x_init[1], cth = x_init[2], cv = x_init[3];
+    float cs_, cc_;
+    sincosf(cth, &cs_, &cc_);
+    const float kth = D.k_turn * dt;  // 1 / L
+    float lc = 0.0f;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const bool valid = t < T;
+      const float2 v = valid ? V[t * vs] : make_float2(0.0f, 0.0f);
+      const float v_a = cv + warp_incl_scan(v.y * dt, lane);  // v_{t+1}
+      const float v_b = from_prev_lane(v_a, cv, lane);       // v_t
+      const float th_a = cth + warp_incl_scan(v_b * tanf(v.x) * kth, lane);
+      float sa, ca;
+      sincosf(th_a, &sa, &ca);
+      const float cb = from_prev_lane(ca, cc_, lane), sb = from_prev_lane(sa, cs_, lane);
+      const float vdt = v_b * dt;
+      const float xa = cx + warp_incl_scan(vdt * cb, lane);
+      const float ya = cy + warp_incl_scan(vdt * sb, lane);
+      if (x1 && t == 0) {
+        x1[0] = xa;
+        x1[1] = ya;
+        x1[2] = th_a;
+        x1[3] = v_a;
+      }
+      if (valid) {
+        pose[t * ps] = make_float4(xa, ya, ca, sa);
+        if constexpr (COST) {
+          const float xs[4] = {xa, ya, th_a, v_a};
+          const float* xr = xrf + (t + 1) * 4;
+          float q = 0.0f;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) {
+            const float e = xs[d] - xr[d];
+            q = fmaf(D.Q[d] * e, e, q);
+          }
+          const float2 u = Uf[t], a = Af[t];
+          lc += fmaf(a.x, v.x - u.x, fmaf(a.y, v.y - u.y, q));
+          if (t == T - 1) {
+            const float* xT = xrf + T * 4;
+            float f = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              const float e = xs[d] - xT[d];
+              f = fmaf(D.Qf[d] * e, e, f);
+            }
+            lc += f;
+          }
+        }
+      }
+      cv = lane31(v_a);
+      cth = lane31(th_a);
+      cc_ = lane31(ca);
+      cs_ = lane31(sa);
+      cx = lane31(xa);
+      cy = lane31(ya);
+    }
+    if constexpr (COST) ff_add(cost, lc);
+  } else if constexpr (MODEL == 3) {
+    // the paper's planar quadrotor (Eq. 12): pitch (rate omega) -> (cos,
+    // sin) -> velocities (thrust m g + u_t) -> position
+    float cx = x_init[0], cz = x_init[1], cth = x_init[2];
+    float cvx = x_init[3], cvz = x_init[4];
+    float cs_, cc_;
+    sincosf(cth, &cs_, &cc_);
+    float lc = 0.0f;
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const bool valid = t < T;
+      const float2 v = valid ? V[t * vs] : make_float2(0.0f, 0.0f);
+      const float th_a = cth + warp_incl_scan(v.x * dt, lane);  // theta_{t+1}
+      float sa, ca;
+      sincosf(th_a, &sa, &ca);
+      const float cb = from_prev_lane(ca, cc_, lane), sb = from_prev_lane(sa, cs_, lane);
+      const float acc = fmaf(v.y, D.inv_mass, D.g);  // (m g + u_t) / m
+      const float vx_a = cvx + warp_incl_scan(-acc * sb * dt, lane);
+      const float vz_a = cvz + warp_incl_scan(fmaf(acc, cb, -D.g) * dt, lane);
+      const float vx_b = from_prev_lane(vx_a, cvx, lane), vz_b = from_prev_lane(vz_a, cvz, lane);
+      const float x_a = cx + warp_incl_scan(vx_b * dt, lane);
+      const float z_a = cz + warp_incl_scan(vz_b * dt, lane);
+      if (x1 && t == 0) {
+        x1[0] = x_a;
+        x1[1] = z_a;
+        x1[2] = th_a;
+        x1[3] = vx_a;
+        x1[4] = vz_a;
+      }
+      if (valid) {
+        pose[t * ps] = make_float4(x_a, z_a, ca, sa);
+        if constexpr (COST) {
+          const float xs[5] = {x_a, z_a, th_a, vx_a, vz_a};
+          const float* xr = xrf + (t + 1) * 5;
+          float q = 0.0f;
+#pragma unroll
+          for (int d = 0; d < 5; ++d) {
+            const float e = xs[d] - xr[d];
+            q = fmaf(D.Q[d] * e, e, q);
+          }
+          const float2 u = Uf[t], a = Af[t];
+          lc += fmaf(a.x, v.x - u.x, fmaf(a.y, v.y - u.y, q));
+          if (t == T - 1) {
+            const float* xT = xrf + T * 5;
+            float f = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+              const float e = xs[d] - xT[d];
+              f = fmaf(D.Qf[d] * e, e, f);
+            }
+            lc += f;
+          }
+        }
+      }
+      cth = lane31(th_a);
+      cc_ = lane31(ca);
+      cs_ = lane31(sa);
+      cvx = lane31(vx_a);
+      cvz = lane31(vz_a);
+      cx = lane31(x_a);
+      cz = lane31(z_a);
+    }
+    if constexpr (COST) ff_add(cost, lc);
   } else {
     float cy = x_init[0], cz = x_init[1], cph = x_init[2];
     float cvy = x_init[3], cvz = x_init[4], cw = x_init[5];
     float cs_, cc_;
     sincosf(cph, &cs_, &cc_);
-    const float kw = D.arm_over_I * dt;
+    const float kw = D.k_turn * dt;  // arm / I
     float lc = 0.0f;
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;

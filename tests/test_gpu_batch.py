@@ -166,20 +166,24 @@ def test_batch_autotuned_policy_shapes_and_equals_alone(gpu):
                 np.testing.assert_array_equal(u_b[i], g.get_control())
 
 
-@pytest.mark.parametrize("model,npos", [("unicycle", 8), ("unicycle", 14), ("quad", 8), ("quad", 14)])
+@pytest.mark.parametrize("model,npos", [("unicycle", 8), ("unicycle", 14), ("quad", 8), ("quad", 14),
+                                        ("ackermann", 8), ("ackermann", 14), ("quad5", 8)])
 def test_register_forms_equal_bitwise(gpu, model, npos):
     """A controller whose grid spans several waves runs the 80-register form
     of the step kernel; a one-wave controller the 96-register form.  The
     80-register controller gives, bit for bit, what the batch kernel gives
     for it at the same launch shape (and the batch kernel equals the
-    96-register form in the test above).  Both models, 8 and 14 points per
-    barrier thread."""
+    96-register form in the test above).  All four models, 8 and 14 points
+    per barrier thread."""
     if model == "unicycle":
         w = W.unicycle_stress(3, K=16384, T=40)
         small = W.unicycle_stress(3, K=512, T=40)
-    else:
+    elif model == "quad":
         w = W.quad2d(3, K=16384, T=30)
         small = W.quad2d(3, K=512, T=30)
+    else:
+        w = W.PRESETS[model](3, K=16384, T=30)
+        small = W.PRESETS[model](3, K=512, T=30)
     shape = dict(samples_per_cta=20, threads=256, positions_per_thread=npos)
     with gpu.Controller(small.params, tiling=shape) as g:
         g.set_obstacles(small.obstacles)
@@ -200,3 +204,26 @@ def test_register_forms_equal_bitwise(gpu, model, npos):
             np.testing.assert_array_equal(u_b[0], u0)
             np.testing.assert_array_equal(st["U"], U)
             np.testing.assert_array_equal(st["costs"], d["costs"])
+
+
+def test_batch_all_four_models_equal_alone(gpu):
+    """One batched launch holding all four models (unicycle, 6-state
+    quadrotor, Ackermann vehicle, 5-state quadrotor): each controller's
+    result equals, bit for bit, its step alone at the same launch shape."""
+    worlds = [W.unicycle_small(1), W.quad2d(1, K=1024, T=20), W.ackermann(1), W.quad5(1)]
+    with gpu.Batch(8, 256 << 20) as b:
+        slots = [b.add(w.params, w.obstacles) for w in worlds]
+        shapes = [b.slot_info(s) for s in slots]
+        b.step(slots, [w.x_start for w in worlds], [w.reference(w.x_start) for w in worlds])
+        u_b = b.controls()
+        st_b = [b.state(s) for s in slots]
+    for i, (w, sh) in enumerate(zip(worlds, shapes)):
+        with gpu.Controller(w.params, tiling=dict(samples_per_cta=sh["samples_per_cta"], threads=256,
+                                                  positions_per_thread=sh["positions_per_thread"])) as g:
+            g.set_obstacles(w.obstacles)
+            g.step(w.x_start, w.reference(w.x_start))
+            u0, U = g.get_control(want_U=True)
+            d = g.get_debug()
+        np.testing.assert_array_equal(u_b[i], u0)
+        np.testing.assert_array_equal(st_b[i]["U"], U)
+        np.testing.assert_array_equal(st_b[i]["costs"], d["costs"])

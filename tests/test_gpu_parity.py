@@ -322,3 +322,21 @@ def test_back_to_back_steps_without_sync(gpu):
         ub, Ub = b.get_control(want_U=True)
         np.testing.assert_array_equal(ua, ub)
         np.testing.assert_array_equal(Ua, Ub)
+
+
+@pytest.mark.parametrize("name", ["ackermann", "quad5"])
+def test_paper_models_closed_loop(gpu, orc, name):
+    """The paper's own plant models (Eq. 14 vehicle with 8 shape points,
+    Eq. 12 five-state quadrotor with 7) on their mission presets, three
+    receding-horizon steps, every sample compared."""
+    run_pair(gpu, orc, W.PRESETS[name](0), steps=3)
+
+
+@pytest.mark.parametrize("name", ["ackermann", "quad5"])
+def test_paper_models_ragged_and_large(gpu, orc, name):
+    """Ragged tiles (K not a multiple of the tile) and a grid of several
+    waves, in the launch shapes a user would get by default."""
+    w = W.PRESETS[name](1, K=777, T=23)
+    run_pair(gpu, orc, w, steps=1, tiling=dict(samples_per_cta=13, threads=128,
+                                               positions_per_thread=8))
+    run_pair(gpu, orc, W.PRESETS[name](2, K=16384, T=30), steps=1)

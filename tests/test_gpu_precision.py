@@ -38,7 +38,7 @@ def gpu():
     return binding
 
 
-@pytest.mark.parametrize("name", ["unicycle_small", "quad2d", "unicycle_stress"])
+@pytest.mark.parametrize("name", ["unicycle_small", "quad2d", "unicycle_stress", "ackermann", "quad5"])
 def test_precision_against_oracle(gpu, orc, name):
     """In the launch shape bench.py times for the workload (the autotuner's
     pick)."""
