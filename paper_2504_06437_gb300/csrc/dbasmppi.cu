@@ -208,7 +208,7 @@ int max_smem_optin() {
 // Step kernel of a launch: the 96-register form, or the 80-register form
 // (_r80) when the grid spans more than one wave of the 96-register form and
 // the lower cap raises the CTAs resident per SM.  The shared-memory limit
-// of every step kernel is raised once per device; the last decision per
+// of a model's step kernels is raised once per device; the last decision per
 // device is kept, so a repeated configuration costs no occupancy query
 // (the allocation-free entry point calls this every step).
 constexpr int kMaxPickDevices = 64;
@@ -217,7 +217,7 @@ struct PickMemo {
   StepFn fn;
 };
 std::mutex g_pick_mu;
-bool g_step_attr[kMaxPickDevices] = {false};
+bool g_step_attr[kMaxPickDevices][MPPI_NUM_MODELS] = {};
 PickMemo g_pick_memo[kMaxPickDevices] = {};
 
 int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, StepFn* out) {
@@ -225,14 +225,15 @@ int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, S
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxPickDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_pick_mu);
-  if (!g_step_attr[dev]) {
+  // only this model's kernels: with lazy module loading, touching a kernel
+  // loads its module, and the models a process never steps stay unloaded
+  if (!g_step_attr[dev][model]) {
     const int lim = max_smem_optin();
-    for (int m = 0; m < MPPI_NUM_MODELS; ++m)
-      for (int np : {8, 14})
-        for (bool r80 : {false, true})
-          CK(cudaFuncSetAttribute(pick_kernel(m, np, r80),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    g_step_attr[dev] = true;
+    for (int np : {8, 14})
+      for (bool r80 : {false, true})
+        CK(cudaFuncSetAttribute(pick_kernel(model, np, r80),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    g_step_attr[dev][model] = true;
   }
   PickMemo& m = g_pick_memo[dev];
   if (m.fn && m.model == model && m.npos == npos && m.threads == threads && m.smem == smem &&
