@@ -63,6 +63,7 @@ class _Params(C.Structure):
         ("mass", C.c_double), ("inertia", C.c_double),
         ("arm", C.c_double), ("gravity", C.c_double),
         ("wheelbase", C.c_double),
+        ("sgf_window", C.c_int32), ("sgf_order", C.c_int32),
     ]
 
 
@@ -112,6 +113,8 @@ def _load():
                                          C.POINTER(_State), C.POINTER(C.c_int32), C.c_int32,
                                          dp, C.POINTER(C.c_uint8), dp]
         lib.orc_sample_costs.restype = C.c_int
+        lib.orc_sgf.argtypes = [dp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, dp,
+                                C.c_int32]
         lib.orc_set_threads.argtypes = [C.c_int]
         lib.orc_get_threads.restype = C.c_int
         _lib = lib
@@ -238,6 +241,26 @@ def weights(S, lam: float):
     return w, rho, Z.value
 
 
+def sgf(y, window: int, order: int) -> np.ndarray:
+    """Savitzky-Golay smoothing of each column of ``y`` (T, or T x m) along
+    its first axis (Algorithm 1's SGF): at each t the degree-``order``
+    least-squares polynomial through the window around t (the first or last
+    ``window`` samples near the ends), evaluated at t."""
+    lib = _load()
+    y = _f64(y)
+    Y = y.reshape(y.shape[0], -1)
+    out = np.zeros_like(Y)
+    T, m = Y.shape
+    if not (window % 2 == 1 and 0 <= order < window <= T and order <= 6):
+        raise ValueError("need an odd window, order < window <= T, order <= 6")
+    for d in range(m):
+        col = np.ascontiguousarray(Y[:, d])
+        o = np.zeros(T)
+        lib.orc_sgf(_dp(col), 1, T, window, order, _dp(o), 1)
+        out[:, d] = o
+    return out.reshape(y.shape)
+
+
 def set_threads(n: int) -> None:
     _load().orc_set_threads(int(n))
 
@@ -293,6 +316,9 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
                Ustar=_dp(res["Ustar"]), u0=_dp(res["u0"]))
     rc = lib.orc_step(C.byref(p), _dp(ob), ob.shape[0], _dp(x0), _dp(xref),
                       C.byref(st), C.byref(out))
+    if rc == -2:
+        raise ValueError("sgf_window must be 0 or odd and <= T, with sgf_order < "
+                         "sgf_window and <= 6")
     if rc != 0:
         raise MemoryError("oracle step failed to allocate")
     res.update(CB_star=out.CB_star, beta_used=out.beta_used, beta_d=out.beta_d,

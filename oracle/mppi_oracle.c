@@ -22,6 +22,8 @@
  *   Eq. 13/15 h = |p_i - c_j|^2 - r_j^2 over shape points and obstacles
  *   Alg. 1  the outer-loop body: sample, roll out, weight, update, actuate,
  *           nominal rollout for C_B, S_e, shift.
+ *   Alg. 1  SGF: Savitzky-Golay smoothing of the weighted perturbation
+ *           (Sec. III-A, last paragraph)                -> orc_sgf, orc_step
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11), counter (k, t, iter_lo,
@@ -73,6 +75,8 @@ typedef struct {
   uint64_t seed;
   double mass, inertia, arm, gravity; /* quadrotor constants */
   double wheelbase;                   /* L of Eq. 14 */
+  int32_t sgf_window, sgf_order;      /* Savitzky-Golay smoothing of the
+                                         update (Algorithm 1); window 0 = off */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -340,6 +344,75 @@ double orc_weights(const double* S, int32_t K, double lambda, double* w,
   return rho;
 }
 
+/* Savitzky-Golay smoothing (Algorithm 1: U* = U + SGF(weighted
+ * perturbation); Sec. III-A names the filter but gives no window or order).
+ * Reading: y holds T samples (element t at y[t * stride]); out[t] is the
+ * value at t of the degree-`order` polynomial fitted by least squares to the
+ * W samples of the window centred on t, or, within W/2 of an end, to the
+ * first or last W samples (the fit is evaluated off centre there).  Needs W
+ * odd, order < W <= T.
+ * Written as the definition: per t, the normal equations of the fit on the
+ * window's abscissae scaled to [-1, 1], solved by Gaussian elimination with
+ * partial pivoting, then the polynomial evaluated at t.  The polynomial is
+ * written in the Legendre basis P_0..P_order (Bonnet's recurrence), which
+ * spans the same polynomials as the monomials and keeps the normal matrix
+ * close to diagonal on [-1, 1]. */
+static void legendre_row(double z, int m, double* P) {
+  P[0] = 1.0;
+  if (m > 1) P[1] = z;
+  for (int k = 1; k + 1 < m; ++k) P[k + 1] = ((2 * k + 1) * z * P[k] - k * P[k - 1]) / (k + 1);
+}
+
+#define ORC_SGF_MAXORDER 6
+void orc_sgf(const double* y, int32_t stride, int32_t T, int32_t W,
+             int32_t order, double* out, int32_t out_stride) {
+  const int m = order + 1, h = W / 2;
+  const double c = 0.5 * (W - 1);
+  for (int t = 0; t < T; ++t) {
+    int s = t - h;
+    if (s < 0) s = 0;
+    if (s > T - W) s = T - W;
+    double A[ORC_SGF_MAXORDER + 1][ORC_SGF_MAXORDER + 2];
+    for (int r = 0; r < m; ++r)
+      for (int q = 0; q <= m; ++q) A[r][q] = 0.0;
+    for (int i = 0; i < W; ++i) {
+      const double yi = y[(size_t)(s + i) * stride];
+      double P[ORC_SGF_MAXORDER + 1];
+      legendre_row((i - c) / c, m, P);
+      for (int r = 0; r < m; ++r) {
+        for (int q = 0; q < m; ++q) A[r][q] += P[r] * P[q];
+        A[r][m] += P[r] * yi;
+      }
+    }
+    for (int col = 0; col < m; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < m; ++r)
+        if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+      if (piv != col)
+        for (int q = 0; q <= m; ++q) {
+          double tmp = A[col][q];
+          A[col][q] = A[piv][q];
+          A[piv][q] = tmp;
+        }
+      for (int r = col + 1; r < m; ++r) {
+        const double f = A[r][col] / A[col][col];
+        for (int q = col; q <= m; ++q) A[r][q] -= f * A[col][q];
+      }
+    }
+    double a[ORC_SGF_MAXORDER + 1];
+    for (int r = m - 1; r >= 0; --r) {
+      double v = A[r][m];
+      for (int q = r + 1; q < m; ++q) v -= A[r][q] * a[q];
+      a[r] = v / A[r][r];
+    }
+    double P[ORC_SGF_MAXORDER + 1];
+    legendre_row(((t - s) - c) / c, m, P);
+    double v = 0.0;
+    for (int k = 0; k < m; ++k) v += a[k] * P[k];
+    out[(size_t)t * out_stride] = v;
+  }
+}
+
 /* Per-controller state carried between iterations. */
 typedef struct {
   double* U;      /* T x 2 nominal control sequence (in/out) */
@@ -375,11 +448,16 @@ int orc_get_threads(void) {
 }
 
 /* One Algorithm 1 outer-loop body.  xref is (T+1) x n.
- * Returns 0, or -1 on allocation failure. */
+ * Returns 0, -1 on allocation failure, -2 for smoothing parameters that
+ * orc_sgf does not accept. */
 int orc_step(const orc_params* p, const double* obst, int32_t J,
              const double* x0, const double* xref, orc_state* st,
              orc_out* out) {
   const int K = p->K, T = p->T, n = state_dim(p->model);
+  if (p->sgf_window != 0 &&
+      (p->sgf_window % 2 != 1 || p->sgf_window > T || p->sgf_order < 0 ||
+       p->sgf_order >= p->sgf_window || p->sgf_order > ORC_SGF_MAXORDER))
+    return -2;
   double* S = (double*)malloc(sizeof(double) * K);
   uint8_t* coll = (uint8_t*)malloc(K);
   double* minh = (double*)malloc(sizeof(double) * K);
@@ -419,15 +497,29 @@ int orc_step(const orc_params* p, const double* obst, int32_t J,
                    st->iter, k, Minv, &S[k], &coll[k], &minh[k],
                    du + (size_t)k * T * 2);
 
-  /* Eq. 4: weights and the weighted perturbation. */
+  /* Eq. 4: weights and the weighted perturbation dU (held in Us), then
+   * Algorithm 1's U* = U + SGF(dU), clamped to the box of Eq. 2. */
   double Z;
   double rho = orc_weights(S, K, p->lambda, w, &Z);
   for (int t = 0; t < T; ++t)
     for (int d = 0; d < 2; ++d) {
       nsum acc = {0.0, 0.0};
       for (int k = 0; k < K; ++k) nsum_add(&acc, w[k] * du[(size_t)k * T * 2 + 2 * t + d]);
-      Us[2 * t + d] = clampd(st->U[2 * t + d] + nsum_get(&acc), p->u_min[d], p->u_max[d]);
+      Us[2 * t + d] = nsum_get(&acc);
     }
+  if (p->sgf_window > 0) {
+    double* raw = (double*)malloc(sizeof(double) * T * 2);
+    if (!raw) {
+      free(S); free(coll); free(minh); free(w); free(du); free(Us);
+      return -1;
+    }
+    memcpy(raw, Us, sizeof(double) * T * 2);
+    for (int d = 0; d < 2; ++d) orc_sgf(raw + d, 2, T, p->sgf_window, p->sgf_order, Us + d, 2);
+    free(raw);
+  }
+  for (int t = 0; t < T; ++t)
+    for (int d = 0; d < 2; ++d)
+      Us[2 * t + d] = clampd(st->U[2 * t + d] + Us[2 * t + d], p->u_min[d], p->u_max[d]);
 
   /* Nominal rollout of U* (Algorithm 1, "for t = 1..T") for C_B(X*). */
   double x[ORC_MAXN], xn[ORC_MAXN];

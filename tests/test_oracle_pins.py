@@ -549,6 +549,99 @@ def test_lambda_limits_on_update(orc):
         np.testing.assert_allclose(r["Ustar"], expect, rtol=0, atol=1e-9)
 
 
+# ------------------------------------------- Savitzky-Golay (Algorithm 1)
+
+@pytest.mark.parametrize("window,order", [(3, 0), (3, 1), (5, 2), (5, 3), (7, 2), (7, 4),
+                                          (11, 3), (11, 6), (21, 4), (21, 6)])
+def test_sgf_matches_scipy_interp(orc, window, order):
+    """Against scipy.signal.savgol_filter's 'interp' mode (least-squares fit
+    of the first / last window at the ends), an independent implementation,
+    at T = window, window + 1 and 40."""
+    signal = pytest.importorskip("scipy.signal")
+    g = np.random.default_rng(window * 10 + order)
+    for T in sorted({window, window + 1, 40}):
+        y = g.normal(size=(T, 2))
+        np.testing.assert_allclose(orc.sgf(y, window, order),
+                                   signal.savgol_filter(y, window, order, axis=0, mode="interp"),
+                                   rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("window,order,num,den", [
+    (5, 2, [-3, 12, 17, 12, -3], 35),
+    (7, 2, [-2, 3, 6, 7, 6, 3, -2], 21),
+    (9, 2, [-21, 14, 39, 54, 59, 54, 39, 14, -21], 231),
+    (7, 4, [5, -30, 75, 131, 75, -30, 5], 231),
+    (5, 3, [-3, 12, 17, 12, -3], 35),   # odd order adds nothing at the centre
+])
+def test_sgf_classic_convolution_coefficients(orc, window, order, num, den):
+    """Away from the ends the filter is a convolution whose weights are the
+    classic Savitzky-Golay smoothing coefficients (Savitzky and Golay,
+    Anal. Chem. 36 (1964), smoothing tables): the response to a unit impulse
+    at t0 read over the window around it."""
+    T, t0, h = 31, 15, window // 2
+    y = np.zeros(T)
+    y[t0] = 1.0
+    out = orc.sgf(y, window, order)
+    np.testing.assert_allclose(out[t0 - h:t0 + h + 1], np.array(num) / den, rtol=0, atol=1e-14)
+    assert np.all(out[:t0 - h] == 0) and np.all(out[t0 + h + 1:] == 0)
+
+
+@pytest.mark.parametrize("window,order", [(3, 1), (5, 2), (9, 4), (21, 6), (63, 6), (63, 3)])
+def test_sgf_reproduces_polynomials(orc, window, order):
+    """A polynomial of degree <= order is its own least-squares fit, so the
+    filter returns it unchanged at every t, the ends included."""
+    g = np.random.default_rng(order)
+    for T in (window, window + 2, 80):
+        t = np.arange(T) / T
+        y = np.stack([np.polyval(g.normal(size=order + 1), t) for _ in range(2)], axis=1)
+        np.testing.assert_allclose(orc.sgf(y, window, order), y, rtol=0, atol=1e-12)
+
+
+def test_sgf_full_order_is_identity_and_order_zero_is_mean(orc):
+    """order = window - 1 interpolates (identity); order 0 is the moving
+    average inside and the mean of the first / last window at the ends."""
+    g = np.random.default_rng(5)
+    y = g.normal(size=(23, 2))
+    np.testing.assert_allclose(orc.sgf(y, 7, 6), y, rtol=0, atol=1e-12)
+    out = orc.sgf(y, 5, 0)
+    for t in range(23):
+        s = min(max(t - 2, 0), 23 - 5)
+        np.testing.assert_allclose(out[t], y[s:s + 5].mean(axis=0), rtol=0, atol=1e-15)
+
+
+def test_step_with_sgf_smooths_the_update(orc):
+    """One iteration with the filter on: the sampled costs and weights are
+    those of the unfiltered step, and U* = clamp(U + SGF(sum_k w_k du_eff_k))
+    with the sums written out and scipy's filter."""
+    signal = pytest.importorskip("scipy.signal")
+    w = W.quad2d(2)
+    p = dict(w.params)
+    p.update(K=64, T=15)
+    g = np.random.default_rng(9)
+    U0 = g.uniform(-0.3, 0.3, size=(15, 2))
+    x0 = w.x_start.copy()
+    xref = w.reference(x0)[:16]
+    r0 = orc.step(p, w.obstacles, x0, xref, orc.new_controller(p, u_init=U0))
+    p.update(sgf_window=7, sgf_order=2)
+    r = orc.step(p, w.obstacles, x0, xref, orc.new_controller(p, u_init=U0), want_du=True)
+    np.testing.assert_array_equal(r["costs"], r0["costs"])
+    np.testing.assert_array_equal(r["weights"], r0["weights"])
+    dU = np.zeros((15, 2))
+    for k in range(64):
+        dU += r["weights"][k] * r["du_eff"][k]
+    lo, hi = np.array(p["u_min"]), np.array(p["u_max"])
+    expect = np.clip(U0 + signal.savgol_filter(dU, 7, 2, axis=0, mode="interp"), lo, hi)
+    np.testing.assert_allclose(r["Ustar"], expect, rtol=0, atol=1e-12)
+    assert np.abs(r["Ustar"] - r0["Ustar"]).max() > 1e-6  # the filter did act
+
+
+@pytest.mark.parametrize("window,order", [(4, 1), (17, 2), (5, 5), (9, 7), (-1, 0)])
+def test_step_rejects_bad_sgf(orc, window, order):
+    p = _cfg(K=4, T=15, sgf_window=window, sgf_order=order)
+    with pytest.raises(ValueError):
+        orc.step(p, np.zeros((0, 3)), np.zeros(3), np.zeros((16, 3)), orc.new_controller(p))
+
+
 # ---------------------------------------------------------------- S_e (Eq. 10)
 
 def test_exploration_rate_no_obstacles_equals_mu(orc):
