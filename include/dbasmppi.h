@@ -57,6 +57,8 @@ extern "C" {
 #define MPPI_ACKERMANN 2
 #define MPPI_QUAD5 3
 #define MPPI_NUM_MODELS 4
+#define MPPI_SGF_MAX_WINDOW 63
+#define MPPI_SGF_MAX_ORDER 6
 
 /* Size limits. */
 #define MPPI_MAX_T 256        /* horizon */
@@ -81,7 +83,15 @@ extern "C" {
  * position + R(heading) (sx, sy).  seed keys the Philox4x32-10 generator.
  * mass, inertia, arm, gravity are the quadrotor constants (mass and gravity
  * also for MPPI_QUAD5); wheelbase is L of Eq. 14 (MPPI_ACKERMANN, > 0, whose
- * steering limits must lie inside (-pi/2, pi/2)). */
+ * steering limits must lie inside (-pi/2, pi/2)).
+ * sgf_window, sgf_order: Savitzky-Golay smoothing of the weighted
+ * perturbation before it is added (Algorithm 1, U* = U + SGF(...); the paper
+ * gives no window or order).  0 leaves the update unsmoothed.  Otherwise
+ * each control channel of the T x 2 update is replaced, at every t, by the
+ * value at t of the degree-sgf_order least-squares polynomial through the
+ * sgf_window steps centred on t, or through the first or last sgf_window
+ * steps within sgf_window / 2 of an end.  sgf_window odd, 3..MPPI_SGF_MAX_WINDOW
+ * and <= T; 0 <= sgf_order < sgf_window, sgf_order <= MPPI_SGF_MAX_ORDER. */
 typedef struct mppi_params {
   int32_t model;
   int32_t K, T;
@@ -99,6 +109,7 @@ typedef struct mppi_params {
   uint64_t seed;
   double mass, inertia, arm, gravity;
   double wheelbase;
+  int32_t sgf_window, sgf_order;
 } mppi_params;
 
 /* Kernel launch shape.  Zero fields are chosen by the library. */

@@ -17,8 +17,9 @@ _ROOT = os.path.dirname(_HERE)
 _LIB = os.path.join(_HERE, "libdbasmppi.so")
 _SOURCES = ["csrc/dbasmppi.cu", "csrc/k_step_u.cu", "csrc/k_step_q.cu", "csrc/k_step_a.cu",
             "csrc/k_step_p.cu", "csrc/k_step_u_r80.cu", "csrc/k_step_q_r80.cu",
-            "csrc/k_step_a_r80.cu", "csrc/k_step_p_r80.cu", "csrc/k_batch.cu",
-            "csrc/k_batch_all.cu"]
+            "csrc/k_step_a_r80.cu", "csrc/k_step_p_r80.cu", "csrc/k_step_u_sgf.cu",
+            "csrc/k_step_q_sgf.cu", "csrc/k_step_a_sgf.cu", "csrc/k_step_p_sgf.cu",
+            "csrc/k_batch.cu", "csrc/k_batch_all.cu"]
 _DEPS = _SOURCES + ["csrc/mppi_device.cuh", "csrc/mppi_tile.cuh", "csrc/kernels.cuh"]
 HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
 
@@ -96,6 +97,7 @@ class Params(C.Structure):
         ("mass", C.c_double), ("inertia", C.c_double),
         ("arm", C.c_double), ("gravity", C.c_double),
         ("wheelbase", C.c_double),
+        ("sgf_window", C.c_int32), ("sgf_order", C.c_int32),
     ]
 
 

@@ -88,6 +88,16 @@ StepFn pick_kernel(int model, int npos, bool r80) {
   return table[model][npos == 14 ? 1 : 0][r80 ? 1 : 0];
 }
 
+// Step kernels that smooth the update (Savitzky-Golay, 96-register form):
+// separate instantiations, so the kernels above carry no trace of it.
+StepFn pick_sgf_kernel(int model, int npos) {
+  static const StepFn table[MPPI_NUM_MODELS][2] = {{step_u8_sgf, step_u14_sgf},
+                                                   {step_q8_sgf, step_q14_sgf},
+                                                   {step_a8_sgf, step_a14_sgf},
+                                                   {step_p8_sgf, step_p14_sgf}};
+  return table[model][npos == 14 ? 1 : 0];
+}
+
 // World points a barrier thread holds: whole units of P points each; the
 // instantiated sizes are 8, 14 and 16, picked to waste the fewest slots.
 int pick_npos(int P) {
@@ -168,7 +178,23 @@ int validate(const mppi_params* p) {
     if (!(p->u_min[0] > -1.5707963267948966 && p->u_max[0] < 1.5707963267948966))
       return fail(MPPI_EINVAL, "steering limits must lie inside (-pi/2, pi/2)");
   }
+  if (p->sgf_window != 0) {
+    const int w = p->sgf_window, o = p->sgf_order;
+    if (w < 3 || w % 2 != 1 || w > MPPI_SGF_MAX_WINDOW || w > p->T)
+      return fail(MPPI_EINVAL, "sgf_window=%d must be 0 or odd in [3, min(%d, T)]", w,
+                  MPPI_SGF_MAX_WINDOW);
+    if (o < 0 || o >= w || o > MPPI_SGF_MAX_ORDER)
+      return fail(MPPI_EINVAL, "sgf_order=%d must be in [0, min(%d, sgf_window - 1)]", o,
+                  MPPI_SGF_MAX_ORDER);
+  }
   return MPPI_OK;
+}
+
+// Bytes of the buffer of the barrier weights cw: T floats, then, when the
+// update is smoothed, the W x W Savitzky-Golay weights (sgf_table_offset).
+size_t cw_bytes(const mppi_params* p) {
+  if (p->sgf_window <= 0) return sizeof(float) * (size_t)p->T;
+  return sizeof(float) * ((size_t)sgf_table_offset(p->T) + (size_t)p->sgf_window * p->sgf_window);
 }
 
 // Tiles merged by one CTA: all of them in one level up to 256 tiles, else
@@ -218,13 +244,26 @@ struct PickMemo {
 };
 std::mutex g_pick_mu;
 bool g_step_attr[kMaxPickDevices][MPPI_NUM_MODELS] = {};
+bool g_sgf_attr[kMaxPickDevices][MPPI_NUM_MODELS] = {};
 PickMemo g_pick_memo[kMaxPickDevices] = {};
 
-int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, StepFn* out) {
+int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, bool sgf,
+                       StepFn* out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxPickDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_pick_mu);
+  if (sgf) {
+    if (!g_sgf_attr[dev][model]) {
+      const int lim = max_smem_optin();
+      for (int np : {8, 14})
+        CK(cudaFuncSetAttribute(pick_sgf_kernel(model, np),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+      g_sgf_attr[dev][model] = true;
+    }
+    *out = pick_sgf_kernel(model, npos);
+    return MPPI_OK;
+  }
   // only this model's kernels: with lazy module loading, touching a kernel
   // loads its module, and the models a process never steps stay unloaded
   if (!g_step_attr[dev][model]) {
@@ -266,7 +305,7 @@ struct mppi_ctx {
   double* d_U = nullptr;
   float2* d_cU = nullptr;
   float2* d_cA = nullptr;
-  float* d_cw = nullptr;
+  float* d_cw = nullptr;   // cw, then the smoothing weights when the update is smoothed
   DevState* d_st = nullptr;
   double* d_obst = nullptr;
   double* d_in = nullptr;  // x0 (n) then xref ((T+1) n)
@@ -463,6 +502,7 @@ void fill_desc(mppi_ctx* c) {
   D.coll = c->d_coll;
   D.Ustar = c->d_Ustar;
   D.host_out = c->h_out_dev;  // null for the batch slots and the static entry point
+  D.sgf_wp = p->sgf_window > 0 ? p->sgf_window | (p->sgf_order << 8) : 0;
 }
 
 int check_status(mppi_ctx* c) {
@@ -508,7 +548,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   ALLOC(c->d_U, sizeof(double) * 2 * T);
   ALLOC(c->d_cU, sizeof(float2) * T);
   ALLOC(c->d_cA, sizeof(float2) * T);
-  ALLOC(c->d_cw, sizeof(float) * T);
+  ALLOC(c->d_cw, cw_bytes(p));
   ALLOC(c->d_st, sizeof(DevState));
   ALLOC(c->d_obst, 16);
   c->Jcap = 0;
@@ -554,6 +594,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   c->last = c->own;
   fill_desc(c);
   rc = choose_step_kernel(p->model, c->tl.positions_per_thread, c->tl.threads, c->smem, nTiles,
+                          p->sgf_window > 0,
                           &c->fn);
   if (rc) {
     free_ctx(c);
@@ -616,7 +657,8 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
   if (t.samples_per_cta != c->tl.samples_per_cta)
     return fail(MPPI_EINVAL, "obstacle set too large for the controller's tile shape");
   StepFn fn = nullptr;
-  rc = choose_step_kernel(c->p.model, t.positions_per_thread, t.threads, smem, c->D.nTiles, &fn);
+  rc = choose_step_kernel(c->p.model, t.positions_per_thread, t.threads, smem, c->D.nTiles,
+                          c->p.sgf_window > 0, &fn);
   if (rc) return rc;
   c->tl = t;
   c->smem = smem;
@@ -904,13 +946,14 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   const int GT = group_size(nTiles);
   const int nGroups = (nTiles + GT - 1) / GT;
   StepFn fn = nullptr;  // picked before anything is launched
-  rc = choose_step_kernel(p->model, c.tl.positions_per_thread, c.tl.threads, c.smem, nTiles, &fn);
+  rc = choose_step_kernel(p->model, c.tl.positions_per_thread, c.tl.threads, c.smem, nTiles,
+                          p->sgf_window > 0, &fn);
   if (rc) return rc;
   size_t off = 0;
   const size_t o_st = carve(&off, sizeof(DevState));
   const size_t o_cU = carve(&off, sizeof(float2) * T);
   const size_t o_cA = carve(&off, sizeof(float2) * T);
-  const size_t o_cw = carve(&off, sizeof(float) * T);
+  const size_t o_cw = carve(&off, cw_bytes(p));
   const size_t o_obst = carve(&off, (size_t)align_up(24 * (J > 0 ? J : 1), 16));
   const size_t o_part = carve(&off, sizeof(float) * (size_t)nTiles * 2 * T);
   const size_t o_prz = carve(&off, sizeof(float4) * nTiles);
@@ -1168,7 +1211,7 @@ size_t slot_bytes(const mppi_params* p, const mppi_tiling* t, int Jcap) {
   carve(&off, sizeof(double) * 2 * T);
   carve(&off, sizeof(float2) * T);
   carve(&off, sizeof(float2) * T);
-  carve(&off, sizeof(float) * T);
+  carve(&off, cw_bytes(p));
   carve(&off, sizeof(DevState));
   carve(&off, sizeof(float) * (size_t)nTiles * 2 * T);
   carve(&off, sizeof(float4) * nTiles);
@@ -1193,7 +1236,7 @@ void slot_layout(mppi_batch* b, BatchSlot& s, mppi_ctx* c) {
   c->d_U = (double*)(base + carve(&off, sizeof(double) * 2 * T));
   c->d_cU = (float2*)(base + carve(&off, sizeof(float2) * T));
   c->d_cA = (float2*)(base + carve(&off, sizeof(float2) * T));
-  c->d_cw = (float*)(base + carve(&off, sizeof(float) * T));
+  c->d_cw = (float*)(base + carve(&off, cw_bytes(p)));
   c->d_st = (DevState*)(base + carve(&off, sizeof(DevState)));
   c->d_part = (float*)(base + carve(&off, sizeof(float) * (size_t)nTiles * 2 * T));
   c->d_part_rz = (float4*)(base + carve(&off, sizeof(float4) * nTiles));

@@ -99,6 +99,7 @@ struct CtrlDesc {
   double lambda, inv_lambda, mu_coarse, gamma_ctrl, gamma_bas, R_B_d;
   double umin_d[2], umax_d[2];
   int nscl;
+  int sgf_wp;                // Savitzky-Golay window | order << 8, 0 = off (weights: cw)
   double sigma[4];
   double Lsig[3];            // chol(Sigma): l00, l10, l11
   double Sinv[4];            // gamma * Sigma^-1 (row-major; zero when gamma = 0)
@@ -107,7 +108,8 @@ struct CtrlDesc {
   double* U;                 // T x 2 nominal sequence
   float2* cU;                // T: U in FP32 for the next step
   float2* cA;                // T: gamma Sigma^-1 u_t in FP32 (divided by S_e where used)
-  float* cw;                 // T: R_B c_{t+1}, weight of step t's barrier sum
+  float* cw;                 // T: R_B c_{t+1}, weight of step t's barrier sum (then the
+                             // smoothing weights, see sgf_table_offset)
   DevState* st;
   const double* obst;        // J x 3 (cx, cy, r), padded to 16 bytes
   const double* x0;          // n (may be overridden per launch)
@@ -122,6 +124,11 @@ struct CtrlDesc {
   double* Ustar;             // T x 2
   HostOut* host_out;         // device alias of the host mirror, or null
 };
+
+// The Savitzky-Golay weights (W x W floats, row q: the fit's value at window
+// position q) follow the T barrier weights cw at the next 16-byte boundary
+// of the same buffer, when the controller smooths its update.
+__host__ __device__ inline int sgf_table_offset(int T) { return (T + 3) & ~3; }
 
 // Shared-memory layout of one tile; host and device compute it alike.
 // region: poses (overwritten in place by the unit barrier sums) and clamped

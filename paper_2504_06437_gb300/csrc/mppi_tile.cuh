@@ -16,8 +16,45 @@ constexpr long long kTmaWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 #endif
 
 
+// Savitzky-Golay weights (Algorithm 1's SGF) for a window of W steps and
+// polynomials of degree p: w[q W + i] is the weight of window sample i in
+// the least-squares fit's value at window position q.  The fit is the
+// orthogonal projection onto the polynomials of degree <= p, so
+//   w[q W + i] = sum_{k<=p} G_k(x_q) G_k(x_i) / h_k,
+// with G_k the monic discrete orthogonal (Gram) polynomials on the centred
+// abscissae x = -(W-1)/2 .. (W-1)/2, built by their three-term recurrence
+// G_{k+1}(x) = x G_k(x) - b_k G_{k-1}(x), b_k = k^2 (W^2 - k^2) / (4 (4k^2 - 1)),
+// and h_k = sum_x G_k(x)^2 = b_k h_{k-1}, h_0 = W (the discrete Chebyshev
+// polynomials; e.g. Gorry, Anal. Chem. 62 (1990)).  FP64, one entry per
+// thread; p < W.
+__device__ inline void sgf_weights(float* w, int W, int p, int tid, int nthreads) {
+  const double c = 0.5 * (W - 1), WW = (double)W * W;
+  for (int e = tid; e < W * W; e += nthreads) {
+    const int q = e / W, i = e - q * W;
+    const double xq = q - c, xi = i - c;
+    double gq0 = 1.0, gi0 = 1.0, gq1 = xq, gi1 = xi;  // G_0, G_1
+    double h = W;
+    double acc = 1.0 / h;
+    if (p >= 1) {
+      h *= (WW - 1.0) / 12.0;
+      acc += gq1 * gi1 / h;
+    }
+    for (int k = 1; k < p; ++k) {
+      const double b = (double)k * k * (WW - (double)k * k) / (4.0 * (4.0 * k * k - 1.0));
+      const double gq2 = xq * gq1 - b * gq0, gi2 = xi * gi1 - b * gi0;
+      const int k1 = k + 1;
+      h *= (double)k1 * k1 * (WW - (double)k1 * k1) / (4.0 * (4.0 * k1 * k1 - 1.0));
+      acc += gq2 * gi2 / h;
+      gq0 = gq1; gq1 = gq2;
+      gi0 = gi1; gi1 = gi2;
+    }
+    w[e] = (float)acc;
+  }
+}
+
 // Constants of the controller that never change: the unrolled DBaS weights
-// c_s (scaled by R_B) and their sums.  One CTA, at creation.
+// c_s (scaled by R_B) and their sums, and the smoothing weights.  One CTA, at
+// creation (and on every call of the allocation-free entry point).
 __device__ inline void init_constants(const CtrlDesc& D, int tid, int nthreads) {
   const int T = D.T;
   const double g = D.gamma_bas;
@@ -31,6 +68,8 @@ __device__ inline void init_constants(const CtrlDesc& D, int tid, int nthreads) 
     D.st->g1 = g * (1.0 - gT) / (1.0 - g);
     D.st->csum = (T - D.st->g1) / (1.0 - g);
   }
+  if (D.sgf_wp)
+    sgf_weights(D.cw + sgf_table_offset(T), D.sgf_wp & 0xff, D.sgf_wp >> 8, tid, nthreads);
 }
 
 // Per-step constants that depend only on the controller state (U, S_e), for
@@ -346,6 +385,30 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // Sigma^-1 u_t and sum_t u_t . a'_t) are formed in the same pass as U* and
 // the shift, one step per thread; S_e enters afterwards through L, C0 and
 // the 1 / S_e that the next step applies to a'_t.
+// Algorithm 1's SGF on the merged column sums, in place: hi[2t + d] becomes
+// the smoothed sum and lo[2t + d] zero.  The filter is linear, so smoothing
+// the sums before their common 1 / Z scale is smoothing the update.  Window
+// start s = clamp(t - W/2, 0, T - W); t sits at position t - s of it.
+// buf: 2T floats of free shared memory.  Called by every thread of the CTA.
+__device__ __forceinline__ void sgf_columns(const float* __restrict__ w, int W, int T, float* hi,
+                                           float* lo, float* buf, int tid, int nthreads) {
+  const int ncol = 2 * T, half = W >> 1;
+  __syncthreads();
+  for (int c = tid; c < ncol; c += nthreads) buf[c] = hi[c] + lo[c];
+  __syncthreads();
+  for (int c = tid; c < ncol; c += nthreads) {
+    const int t = c >> 1, d = c & 1;
+    const int s = min(max(t - half, 0), T - W);
+    const float* wq = w + (t - s) * W;
+    const float* y = buf + 2 * s + d;
+    float a = 0.0f;
+    for (int i = 0; i < W; ++i) a = fmaf(wq[i], y[2 * i], a);
+    hi[c] = a;
+    lo[c] = 0.0f;
+  }
+  __syncthreads();
+}
+
 template <int MODEL, int NPOS>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
                             const double* __restrict__ x0g, double* out) {
@@ -466,7 +529,11 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 // one-batch form of merge_partials and the odd row stride of row_stride;
 // the one-controller kernels take the pipelined merge and SP = S.  Both
 // choices were measured per kernel; the results are the same bit for bit.
-template <int MODEL, int NPOS, bool BATCHED>
+// SGF: the Savitzky-Golay pass is compiled in (taken when D.sgf_wp is set).
+// The batch kernels carry it, and the one-controller kernels have a form
+// with it and one without, so that controllers that do not smooth run code
+// with no trace of it.
+template <int MODEL, int NPOS, bool BATCHED, bool SGF = BATCHED>
 __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
                          const double* __restrict__ xrefg, char* smem, TileScratch& ts,
                          uint32_t& mbar_phase, double* u0_out = nullptr) {
@@ -763,6 +830,11 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
     if (!ts.flag) return;
     merge_partials<!BATCHED>(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
                    &ts.Z, col_hi, col_lo, tid, nthreads);
+  }
+  if constexpr (SGF) {
+    if (D.sgf_wp)
+      sgf_columns(D.cw + sgf_table_offset(T), D.sgf_wp & 0xff, T, col_hi, col_lo,
+                  reinterpret_cast<float*>(smem + L.region), tid, nthreads);
   }
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
   final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);

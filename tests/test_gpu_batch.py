@@ -227,3 +227,27 @@ def test_batch_all_four_models_equal_alone(gpu):
         np.testing.assert_array_equal(u_b[i], u0)
         np.testing.assert_array_equal(st_b[i]["U"], U)
         np.testing.assert_array_equal(st_b[i]["costs"], d["costs"])
+
+
+def test_batch_with_smoothing_equals_alone(gpu):
+    """Slots with and without Savitzky-Golay smoothing of the update in one
+    batched launch, each equal bit for bit to its step alone."""
+    worlds = [W.unicycle_small(2), W.quad2d(2, K=1024, T=20), W.ackermann(2), W.quad5(2)]
+    sgf = [(5, 2), (0, 0), (9, 3), (3, 1)]
+    params = [dict(w.params, sgf_window=a, sgf_order=o) for w, (a, o) in zip(worlds, sgf)]
+    with gpu.Batch(8, 256 << 20) as b:
+        slots = [b.add(p, w.obstacles) for p, w in zip(params, worlds)]
+        shapes = [b.slot_info(s) for s in slots]
+        for _ in range(2):
+            b.step(slots, [w.x_start for w in worlds], [w.reference(w.x_start) for w in worlds])
+        u_b = b.controls()
+        st_b = [b.state(s) for s in slots]
+    for i, (w, p, sh) in enumerate(zip(worlds, params, shapes)):
+        with gpu.Controller(p, tiling=dict(samples_per_cta=sh["samples_per_cta"], threads=256,
+                                           positions_per_thread=sh["positions_per_thread"])) as g:
+            g.set_obstacles(w.obstacles)
+            for _ in range(2):
+                g.step(w.x_start, w.reference(w.x_start))
+            u0, U = g.get_control(want_U=True)
+        np.testing.assert_array_equal(u_b[i], u0)
+        np.testing.assert_array_equal(st_b[i]["U"], U)

@@ -6,6 +6,7 @@ max(|S|, 1)), the updated control sequence U* within 1e-5 absolute, the set
 of collided samples identical wherever the oracle's min h is farther than
 H_MARGIN from zero (closer samples are reported, not asserted).  Philox words
 are compared bit for bit."""
+import dataclasses
 import math
 
 import numpy as np
@@ -340,3 +341,55 @@ def test_paper_models_ragged_and_large(gpu, orc, name):
     run_pair(gpu, orc, w, steps=1, tiling=dict(samples_per_cta=13, threads=128,
                                                positions_per_thread=8))
     run_pair(gpu, orc, W.PRESETS[name](2, K=16384, T=30), steps=1)
+
+
+def _smoothed(world, window, order):
+    return dataclasses.replace(world, params=dict(world.params, sgf_window=window,
+                                                  sgf_order=order))
+
+
+@pytest.mark.parametrize("name,window,order", [
+    ("unicycle_small", 5, 2),   # T 30
+    ("quad2d", 11, 3),          # T 50, 7 shape points
+    ("ackermann", 7, 4),        # T 20
+    ("quad5", 3, 0),            # T 20: three-step moving average
+])
+def test_sgf_closed_loop(gpu, orc, name, window, order):
+    """Algorithm 1's SGF on the update: the step's Savitzky-Golay weights
+    (built on the device from the Gram-polynomial recurrence) against the
+    oracle's per-window least-squares fit, three receding-horizon steps on
+    each model, every sample and every U* entry compared."""
+    run_pair(gpu, orc, _smoothed(W.PRESETS[name](4), window, order), steps=3)
+
+
+@pytest.mark.parametrize("T,window,order,tiling", [
+    (21, 21, 2, None),                   # one window for every t
+    (37, 37, 6, None),                   # the widest window T allows, highest order
+    (23, 7, 6, dict(samples_per_cta=13, threads=128, positions_per_thread=8)),  # order W-1
+    (40, 15, 1, dict(samples_per_cta=7, threads=512, positions_per_thread=14)),
+])
+def test_sgf_edges_and_ragged(gpu, orc, T, window, order, tiling):
+    """Windows as wide as the horizon, the highest order, order W - 1 (the
+    identity) and ragged tiles in several launch shapes."""
+    w = _smoothed(W.quad2d(5, K=777, T=T), window, order)
+    run_pair(gpu, orc, w, steps=1, tiling=tiling)
+
+
+def test_sgf_widest_window(gpu, orc):
+    """The largest window the library takes (63 steps) at T = 70."""
+    run_pair(gpu, orc, _smoothed(W.quad2d(6, K=512, T=70), 63, 5), steps=2)
+
+
+def test_sgf_large_grid(gpu, orc):
+    """Several waves of tiles and a two-level merge with smoothing on."""
+    run_pair(gpu, orc, _smoothed(W.quad2d(7, K=16384, T=50), 9, 2), steps=1)
+
+
+@pytest.mark.parametrize("window,order", [(4, 1), (65, 2), (5, 5), (9, 7), (-3, 0), (31, 2)])
+def test_sgf_rejects_bad_parameters(gpu, window, order):
+    """Even, too wide (65 > 63, or 31 > T = 30), negative windows and orders
+    >= window or > 6 are refused at creation with MPPI_EINVAL."""
+    w = _smoothed(W.unicycle_small(0), window, order)
+    with pytest.raises(gpu.MppiError) as e:
+        gpu.Controller(w.params)
+    assert e.value.code == gpu.MPPI_EINVAL

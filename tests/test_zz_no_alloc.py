@@ -21,7 +21,8 @@ U_ATOL = 1e-5
 COST_RTOL = 1e-4
 
 
-def test_step_static_matches_context_api_two_calls():
+@pytest.mark.parametrize("sgf", [(0, 0), (9, 3)])
+def test_step_static_matches_context_api_two_calls(sgf):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -32,7 +33,7 @@ def test_step_static_matches_context_api_two_calls():
                                      vp, vp]
 
     world = W.quad2d(3, K=1024, T=40)
-    p = world.params
+    p = dict(world.params, sgf_window=sgf[0], sgf_order=sgf[1])
     K, T, n = p["K"], p["T"], world.n
     x = world.x_start.copy()
     xref = world.reference(x)
