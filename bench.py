@@ -202,9 +202,16 @@ def whole_job_value(ws, units_per_rank, ms_max):
     return ws * units_per_rank / (ms_max / 1e3)
 
 
-def world_for(workload, seed):
+def world_for(workload, seed, sgf=""):
+    """The named workload; sgf "W,P" turns on Savitzky-Golay smoothing of the
+    update (window W, order P) in its parameters."""
+    import dataclasses
     from paper_2504_06437_gb300 import workloads as W
-    return W.PRESETS[workload](seed)
+    world = W.PRESETS[workload](seed)
+    if sgf:
+        w_, p_ = (int(v) for v in sgf.split(","))
+        world = dataclasses.replace(world, params=dict(world.params, sgf_window=w_, sgf_order=p_))
+    return world
 
 
 def describe(world):
@@ -214,13 +221,15 @@ def describe(world):
             "obstacles": int(world.obstacles.shape[0]), "shape_points": P,
             "model": {0: "unicycle", 1: "planar quadrotor (6 states)", 2: "Ackermann vehicle",
                       3: "planar quadrotor (5 states, the paper's)"}[int(p["model"])],
-            "l2": "flushed between timed steps (256 MB write)"}
+            "l2": "flushed between timed steps (256 MB write)",
+            **({"sgf": {"window": int(p["sgf_window"]), "order": int(p["sgf_order"])}}
+               if int(p.get("sgf_window", 0)) > 0 else {})}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    world = world_for(args.workload, 0)
+    world = world_for(args.workload, 0, args.sgf)
     p = world.params
     n_samples = min(int(p["K"]), args.ref_samples)
     threads = os.cpu_count() or 1
@@ -520,6 +529,8 @@ def main():
     ap.add_argument("--load", type=float, default=0.5)
     ap.add_argument("--plain-robots", type=int, default=100)
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--sgf", default="",
+                    help="W,P: Savitzky-Golay smoothing of the update, window W, order P")
     ap.add_argument("--tiling", default="",
                     help="explicit launch shape S,threads,points (skips the autotuner)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -543,7 +554,7 @@ def main():
 
     torch.cuda.set_device(local)
     binding.load()
-    world = world_for(args.workload, rank)
+    world = world_for(args.workload, rank, args.sgf)
     p = world.params
     K, T, n = int(p["K"]), int(p["T"]), world.n
     P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
