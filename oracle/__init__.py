@@ -64,6 +64,8 @@ class _Params(C.Structure):
         ("arm", C.c_double), ("gravity", C.c_double),
         ("wheelbase", C.c_double),
         ("sgf_window", C.c_int32), ("sgf_order", C.c_int32),
+        ("grid", C.POINTER(C.c_float)), ("grid_nx", C.c_int32), ("grid_ny", C.c_int32),
+        ("grid_ox", C.c_double), ("grid_oy", C.c_double), ("grid_res", C.c_double),
     ]
 
 
@@ -113,6 +115,8 @@ def _load():
                                          C.POINTER(_State), C.POINTER(C.c_int32), C.c_int32,
                                          dp, C.POINTER(C.c_uint8), dp]
         lib.orc_sample_costs.restype = C.c_int
+        lib.orc_grid_h.argtypes = [C.POINTER(_Params), C.c_double, C.c_double]
+        lib.orc_grid_h.restype = C.c_double
         lib.orc_sgf.argtypes = [dp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, dp,
                                 C.c_int32]
         lib.orc_set_threads.argtypes = [C.c_int]
@@ -138,11 +142,13 @@ def state_dim(model: int) -> int:
 
 def make_params(cfg: dict) -> _Params:
     """Marshal a parameter dict (keys as in ``_Params``; ``lambda`` accepted
-    for ``lam``) into the oracle's struct.  Missing arrays default to zero."""
+    for ``lam``) into the oracle's struct.  Missing arrays default to zero.
+    ``grid`` is an ny x nx array of signed distances (the grid map), with
+    ``grid_ox``, ``grid_oy``, ``grid_res``; the struct keeps a reference."""
     p = _Params()
     for name, ctype in _Params._fields_:
         key = "lambda" if name == "lam" else name
-        if key not in cfg:
+        if key not in cfg or name in ("grid", "grid_nx", "grid_ny"):
             continue
         val = cfg[key]
         if hasattr(ctype, "_length_"):
@@ -154,6 +160,13 @@ def make_params(cfg: dict) -> _Params:
             setattr(p, name, val)
     if "shape" in cfg:
         p.n_shape = int(np.asarray(cfg["shape"]).reshape(-1, 2).shape[0])
+    if cfg.get("grid") is not None:
+        g = np.ascontiguousarray(cfg["grid"], dtype=np.float32)
+        if g.ndim != 2 or min(g.shape) < 2:
+            raise ValueError("grid must be ny x nx with nx, ny >= 2")
+        p._grid_ref = g
+        p.grid = g.ctypes.data_as(C.POINTER(C.c_float))
+        p.grid_ny, p.grid_nx = g.shape
     return p
 
 
@@ -203,6 +216,13 @@ def dynamics(cfg: dict, x, v) -> np.ndarray:
     xn = np.zeros(n)
     lib.orc_dynamics(C.byref(p), _dp(x), _dp(v), _dp(xn))
     return xn
+
+
+def grid_h(cfg: dict, px: float, py: float) -> float:
+    """The grid map's h at world point (px, py) (bilinear, clamped)."""
+    lib = _load()
+    p = make_params(cfg)
+    return lib.orc_grid_h(C.byref(p), px, py)
 
 
 def bsum(cfg: dict, obstacles, x):

@@ -20,6 +20,7 @@
  *   Eq. 11  NLN product of a normal and a log-normal  -> orc_noise
  *   Eq. 12  planar quadrotor (6-state two-thrust form of Sec. V-A constants)
  *   Eq. 13/15 h = |p_i - c_j|^2 - r_j^2 over shape points and obstacles
+ *   Sec. V-C  the grid map's h at a shape point          -> orc_grid_h
  *   Alg. 1  the outer-loop body: sample, roll out, weight, update, actuate,
  *           nominal rollout for C_B, S_e, shift.
  *   Alg. 1  SGF: Savitzky-Golay smoothing of the weighted perturbation
@@ -77,6 +78,9 @@ typedef struct {
   double wheelbase;                   /* L of Eq. 14 */
   int32_t sgf_window, sgf_order;      /* Savitzky-Golay smoothing of the
                                          update (Algorithm 1); window 0 = off */
+  const float* grid;                  /* grid map (orc_grid_h), or NULL */
+  int32_t grid_nx, grid_ny;
+  double grid_ox, grid_oy, grid_res;
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -212,6 +216,35 @@ void orc_dynamics(const orc_params* p, const double* x, const double* v,
  * collided = any h_ij <= 0, minh = min h_ij.  The pose is (x[0], x[1]) with
  * heading x[2] for both models; shape point s is placed at
  * position + R(heading) s.  obst is J x 3 (cx, cy, r). */
+/* Grid map (Sec. V-C: the local point cloud is turned into a 2D grid map
+ * for the optimisation; the paper does not say how h is read from it).
+ * Reading: the grid holds signed distances (m) to the nearest obstacle,
+ * negative inside one; sample (i, j) sits at (ox + i res, oy + j res),
+ * stored at grid[j nx + i].  h at a point is the bilinear interpolation of
+ * the four samples around it, the point's grid coordinates first clamped to
+ * [0, nx - 1] x [0, ny - 1] (beyond the map the edge values continue).
+ * Needs nx, ny >= 2. */
+double orc_grid_h(const orc_params* p, double px, double py) {
+  const int nx = p->grid_nx, ny = p->grid_ny;
+  double u = (px - p->grid_ox) / p->grid_res;
+  double v = (py - p->grid_oy) / p->grid_res;
+  if (u < 0.0) u = 0.0;
+  if (u > nx - 1) u = nx - 1;
+  if (v < 0.0) v = 0.0;
+  if (v > ny - 1) v = ny - 1;
+  int i = (int)floor(u), j = (int)floor(v);
+  if (i > nx - 2) i = nx - 2;
+  if (j > ny - 2) j = ny - 2;
+  const double fx = u - i, fy = v - j;
+  const float* g = p->grid;
+  const double g00 = g[(size_t)j * nx + i], g10 = g[(size_t)j * nx + i + 1];
+  const double g01 = g[(size_t)(j + 1) * nx + i], g11 = g[(size_t)(j + 1) * nx + i + 1];
+  return (1.0 - fy) * ((1.0 - fx) * g00 + fx * g10) + fy * ((1.0 - fx) * g01 + fx * g11);
+}
+
+/* The fused barrier of Eq. 13 at state x: over the shape points, the sum of
+ * B(h) = 1 / max(h, h_eps) over the circle obstacles and, when a grid map is
+ * set, one more term per point with the grid's h; collided when any h <= 0. */
 void orc_bsum(const orc_params* p, const double* obst, int32_t J,
               const double* x, double* bsum, int32_t* collided, double* minh) {
   double c = cos(x[2]), s = sin(x[2]);
@@ -226,6 +259,12 @@ void orc_bsum(const orc_params* p, const double* obst, int32_t J,
       double dy = py - obst[3 * j + 1];
       double r = obst[3 * j + 2];
       double h = dx * dx + dy * dy - r * r;
+      if (h <= 0.0) coll = 1;
+      if (h < mh) mh = h;
+      B += 1.0 / (h > p->h_eps ? h : p->h_eps);
+    }
+    if (p->grid) {
+      const double h = orc_grid_h(p, px, py);
       if (h <= 0.0) coll = 1;
       if (h < mh) mh = h;
       B += 1.0 / (h > p->h_eps ? h : p->h_eps);

@@ -288,10 +288,43 @@ def quad5(seed: int = 0, K: int = 1024, T: int = 20, J: int = 3) -> World:
     return World(p, obs, start, goal, v_ref=1.0, name="quad5")
 
 
+def sdf_grid(discs, boxes, ox: float, oy: float, res: float, nx: int, ny: int) -> np.ndarray:
+    """A grid map as a perception stack would hand it over: the exact signed
+    distance (m) from each sample (ox + i res, oy + j res) to the union of
+    the discs (cx, cy, r) and the axis-aligned boxes (x0, y0, x1, y1),
+    negative inside, as an ny x nx float32 array (row j, column i)."""
+    X, Y = np.meshgrid(ox + res * np.arange(nx), oy + res * np.arange(ny))
+    d = np.full((ny, nx), np.inf)
+    for cx, cy, r in np.asarray(discs, dtype=np.float64).reshape(-1, 3):
+        d = np.minimum(d, np.hypot(X - cx, Y - cy) - r)
+    for x0, y0, x1, y1 in np.asarray(boxes, dtype=np.float64).reshape(-1, 4):
+        qx = np.abs(X - 0.5 * (x0 + x1)) - 0.5 * (x1 - x0)
+        qy = np.abs(Y - 0.5 * (y0 + y1)) - 0.5 * (y1 - y0)
+        outside = np.hypot(np.maximum(qx, 0.0), np.maximum(qy, 0.0))
+        d = np.minimum(d, outside + np.minimum(np.maximum(qx, qy), 0.0))
+    return d.astype(np.float32)
+
+
+def ackermann_grid(seed: int = 0, K: int = 1024, T: int = 20, res: float = 0.1) -> World:
+    """The vehicle mission with its obstacles given as a grid map instead of
+    circles (Sec. V-C: the vehicle plans on a 2D grid map built from its
+    LiDAR point cloud).  The circles of the ``ackermann`` preset plus the
+    corridor's two walls, rasterised as a signed-distance grid over the
+    100 m x 30 m corridor at ``res`` (0.1 m: 1001 x 301 samples); no circle
+    obstacles are passed."""
+    w = ackermann(seed, K=K, T=T)
+    nx, ny = int(round(100.0 / res)) + 1, int(round(30.0 / res)) + 1
+    walls = [(-5.0, -5.0, 105.0, 0.5), (-5.0, 29.5, 105.0, 35.0)]
+    g = sdf_grid(w.obstacles, walls, 0.0, 0.0, res, nx, ny)
+    p = dict(w.params, grid=g, grid_ox=0.0, grid_oy=0.0, grid_res=res)
+    return World(p, np.zeros((0, 3)), w.x_start, w.goal, w.v_ref, name="ackermann_grid")
+
+
 PRESETS = {
     "unicycle_small": unicycle_small,
     "quad2d": quad2d,
     "unicycle_stress": unicycle_stress,
     "ackermann": ackermann,
     "quad5": quad5,
+    "ackermann_grid": ackermann_grid,
 }

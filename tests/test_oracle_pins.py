@@ -642,6 +642,93 @@ def test_step_rejects_bad_sgf(orc, window, order):
         orc.step(p, np.zeros((0, 3)), np.zeros(3), np.zeros((16, 3)), orc.new_controller(p))
 
 
+# ------------------------------------------------ grid map (Sec. V-C)
+
+def _grid_cfg(f, ox=-2.0, oy=1.0, res=0.5, nx=9, ny=7, **over):
+    X, Y = np.meshgrid(ox + res * np.arange(nx), oy + res * np.arange(ny))
+    g = f(X, Y).astype(np.float32)
+    assert np.array_equal(g.astype(np.float64), f(X, Y)), "samples must be exact in float32"
+    return _cfg(grid=g, grid_ox=ox, grid_oy=oy, grid_res=res, **over)
+
+
+def test_grid_bilinear_exact_on_affine_fields(orc):
+    """Bilinear interpolation reproduces an affine field exactly inside the
+    map; beyond it the point's grid coordinates are clamped to the edge."""
+    f = lambda x, y: 1.0 + 0.5 * x - 0.25 * y
+    cfg = _grid_cfg(f)
+    g = np.random.default_rng(3)
+    for px, py in g.uniform([-2.0, 1.0], [2.0, 4.0], size=(50, 2)):
+        assert orc.grid_h(cfg, px, py) == pytest.approx(f(px, py), abs=1e-13)
+    for px, py in [(-7.0, 2.0), (9.0, 3.3), (0.3, -4.0), (1.1, 20.0), (-9.0, -9.0)]:
+        cx, cy = min(max(px, -2.0), 2.0), min(max(py, 1.0), 4.0)
+        assert orc.grid_h(cfg, px, py) == pytest.approx(f(cx, cy), abs=1e-13)
+
+
+def test_grid_quadratic_interpolation_error_and_nodes_match_circle(orc):
+    """A grid sampled from the circle barrier h = (x-cx)^2 + (y-cy)^2 - r^2
+    returns, between nodes, h + res^2 (fx (1 - fx) + fy (1 - fy)) (linear
+    interpolation of a square over a cell of width res), and at nodes the
+    grid barrier equals the circle obstacle's barrier exactly."""
+    cx, cy, r = 0.5, 2.5, 0.75
+    f = lambda x, y: (x - cx) ** 2 + (y - cy) ** 2 - r * r
+    cfg = _grid_cfg(f)
+    g = np.random.default_rng(4)
+    for px, py in g.uniform([-2.0, 1.0], [2.0, 4.0], size=(50, 2)):
+        fx = ((px + 2.0) / 0.5) % 1.0
+        fy = ((py - 1.0) / 0.5) % 1.0
+        expect = f(px, py) + 0.25 * (fx * (1 - fx) + fy * (1 - fy))
+        assert orc.grid_h(cfg, px, py) == pytest.approx(expect, abs=1e-12)
+    shape = np.array([[0.0, 0.0], [1.0, 0.5]])  # both land on nodes at heading 0
+    for x in ([-1.5, 1.5, 0.0], [0.0, 2.0, 0.0], [0.5, 3.0, 0.0]):
+        c_grid = dict(cfg, shape=shape)
+        c_circ = dict(_cfg(shape=shape))
+        bg = orc.bsum(c_grid, np.zeros((0, 3)), x)
+        bc = orc.bsum(c_circ, np.array([[cx, cy, r]]), x)
+        assert bg[0] == pytest.approx(bc[0], rel=1e-14)
+        assert bg[1] == bc[1] and bg[2] == pytest.approx(bc[2], abs=1e-14)
+
+
+def test_grid_and_circles_add(orc):
+    """With both a grid map and circles, the barrier is the sum of the two
+    barriers, collided if either collides, min h the smaller."""
+    cfg = _grid_cfg(lambda x, y: 0.25 + 0.0 * x + 0.5 * (y - 1.0), shape=[[0.0, 0.0], [0.25, 0.5]])
+    circles = np.array([[0.0, 2.0, 0.5], [1.0, 3.0, 0.25]])
+    for x in ([0.3, 1.2, 0.4], [-0.2, 2.9, -1.0], [0.9, 3.0, 0.0]):
+        both = orc.bsum(cfg, circles, x)
+        grid = orc.bsum(cfg, np.zeros((0, 3)), x)
+        circ = orc.bsum(dict(cfg, grid=None), circles, x)
+        assert both[0] == pytest.approx(grid[0] + circ[0], rel=1e-14)
+        assert both[1] == (grid[1] or circ[1])
+        assert both[2] == min(grid[2], circ[2])
+
+
+def test_grid_collision_inside(orc):
+    """A shape point where the signed distance is negative collides."""
+    cfg = _grid_cfg(lambda x, y: x - 0.5 + 0.0 * y, shape=[[0.0, 0.0]])
+    assert orc.bsum(cfg, np.zeros((0, 3)), [0.25, 2.0, 0.0])[1]
+    assert not orc.bsum(cfg, np.zeros((0, 3)), [0.75, 2.0, 0.0])[1]
+
+
+def test_constant_grid_shifts_every_cost_alike(orc):
+    """A grid of constant distance c adds P / c to the barrier of every
+    state, goal and start included; the DBaS recursion (Eq. 7) is linear in
+    that barrier, so every sample's cost moves by the same amount and the
+    weights and U* do not change."""
+    w = W.ackermann(1)
+    p = dict(w.params)
+    p.update(K=32, T=10)
+    x0 = w.x_start.copy()
+    xref = w.reference(x0)[:11]
+    r0 = orc.step(p, w.obstacles, x0, xref, orc.new_controller(p))
+    g = np.full((4, 5), 2.0, dtype=np.float32)
+    pg = dict(p, grid=g, grid_ox=0.0, grid_oy=0.0, grid_res=30.0)
+    r1 = orc.step(pg, w.obstacles, x0, xref, orc.new_controller(pg))
+    d = r1["costs"] - r0["costs"]
+    assert np.ptp(d) < 1e-9 * np.abs(r0["costs"]).max() and abs(d[0]) > 1.0
+    np.testing.assert_allclose(r1["weights"], r0["weights"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r1["Ustar"], r0["Ustar"], rtol=0, atol=1e-10)
+
+
 # ---------------------------------------------------------------- S_e (Eq. 10)
 
 def test_exploration_rate_no_obstacles_equals_mu(orc):
