@@ -41,8 +41,15 @@ OPS_PER_SAMPLE_STEP = 135  # Philox (~80), NLN map (~20), dynamics + costs (~35)
 L2_FLUSH_BYTES = 256 << 20
 
 
-def algorithmic_ops(K, T, P, J):
-    return K * T * (OPS_PER_PAIR * P * J + OPS_PER_SAMPLE_STEP)
+# grid-map lookup per shape point: grid coordinates (2 subtractions, 2
+# products), 4 clamps, 2 conversions and 2 integer minima, 2 fractions, 3
+# lerps (2 subtractions, 3 fmas), then max, reciprocal, add and min
+OPS_PER_GRID_POINT = 24
+
+
+def algorithmic_ops(K, T, P, J, grid=False):
+    return K * T * (OPS_PER_PAIR * P * J + (OPS_PER_GRID_POINT * P if grid else 0)
+                    + OPS_PER_SAMPLE_STEP)
 
 
 def kernel_src_sha():
@@ -223,7 +230,10 @@ def describe(world):
                       3: "planar quadrotor (5 states, the paper's)"}[int(p["model"])],
             "l2": "flushed between timed steps (256 MB write)",
             **({"sgf": {"window": int(p["sgf_window"]), "order": int(p["sgf_order"])}}
-               if int(p.get("sgf_window", 0)) > 0 else {})}
+               if int(p.get("sgf_window", 0)) > 0 else {}),
+            **({"grid_map": {"nx": int(p["grid"].shape[1]), "ny": int(p["grid"].shape[0]),
+                             "res_m": float(p["grid_res"])}}
+               if p.get("grid") is not None else {})}
 
 
 def run_reference(args, ws, rank):
@@ -567,6 +577,9 @@ def main():
         tiling, tune_us = binding.autotune(p, world.obstacles, iters=10)
     ctl = binding.Controller(p, tiling=tiling)
     ctl.set_obstacles(world.obstacles)
+    has_grid = p.get("grid") is not None
+    if has_grid:
+        ctl.set_grid(p["grid"], p["grid_ox"], p["grid_oy"], p["grid_res"])
     x0 = world.x_start
     xref = world.reference(x0)
     d_in = torch.tensor(np.concatenate([x0, xref.ravel()]), dtype=torch.float64, device="cuda")
@@ -625,11 +638,11 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tops = sms * 128 * f_max / 1e12
-    achieved_tops = algorithmic_ops(K, T, P, J) / (ms_local / 1e3) / 1e12
+    achieved_tops = algorithmic_ops(K, T, P, J, has_grid) / (ms_local / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TOP/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic_per_launch(world.name),
                 "kernel": "step_kernel", "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz",
-                "ops_per_launch": algorithmic_ops(K, T, P, J)}
+                "ops_per_launch": algorithmic_ops(K, T, P, J, has_grid)}
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved_tops / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
     load_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")

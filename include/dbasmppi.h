@@ -64,6 +64,8 @@ extern "C" {
 #define MPPI_MAX_T 256        /* horizon */
 #define MPPI_MAX_K (1 << 22)  /* samples */
 #define MPPI_MAX_OBSTACLES 4096
+#define MPPI_MAX_GRID_SIDE 65535
+#define MPPI_MAX_GRID_SAMPLES (1 << 26)
 #define MPPI_MAX_SHAPE 8      /* shape points per body */
 #define MPPI_MAX_COORD 1.0e6  /* |cx|, |cy| and r of an obstacle, metres */
 #define MPPI_MIN_H_EPS 1.0e-18 /* smallest accepted h_eps */
@@ -141,6 +143,27 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init,
  * |cx|, |cy| or r above MPPI_MAX_COORD).
  * Synchronises with the context's last stream before replacing the set. */
 int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J);
+
+/* Set or remove the grid map (Sec. V-C: the vehicle plans on a 2D grid map
+ * built from its point cloud; the paper does not say how h is read from it).
+ * sdf: ny x nx row-major FP32 signed distances (m) to the nearest obstacle,
+ * negative inside one; sample (i, j) = sdf[j nx + i] lies at
+ * (ox + i res, oy + j res) in the world frame.  The library copies it to
+ * device memory.  Every shape point then adds B(h) = 1 / max(h, h_eps) to
+ * the circle obstacles' terms (Eq. 13), where h is the bilinear
+ * interpolation of the four samples around the point, whose grid coordinates
+ * are first clamped to [0, nx - 1] x [0, ny - 1]; h <= 0 counts as a
+ * collision.  The same holds for the barrier at the goal (beta_d of Eq. 7),
+ * at the measured state and along the nominal rollout.  nx = ny = 0 removes
+ * the map (sdf may then be NULL).  The step launches the grid form of the
+ * kernel while a map is set.  The controller's own API only: batches and
+ * the allocation-free step take circle obstacles.  Errors: MPPI_EINVAL
+ * (a side outside [2, MPPI_MAX_GRID_SIDE], more than MPPI_MAX_GRID_SAMPLES
+ * samples, a non-finite value, origin or cell size, cell size <= 0, NULL
+ * sdf), MPPI_ENOMEM.  Synchronises with the context's last stream before
+ * replacing the map. */
+int mppi_set_grid(mppi_ctx* c, const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
+                  double res);
 
 /* One iteration from host data.  x0: measured state (n doubles).  xref:
  * (T+1) x n reference, row t compared with x_t (row 0 unused), or NULL for

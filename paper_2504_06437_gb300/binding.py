@@ -19,7 +19,8 @@ _SOURCES = ["csrc/dbasmppi.cu", "csrc/k_step_u.cu", "csrc/k_step_q.cu", "csrc/k_
             "csrc/k_step_p.cu", "csrc/k_step_u_r80.cu", "csrc/k_step_q_r80.cu",
             "csrc/k_step_a_r80.cu", "csrc/k_step_p_r80.cu", "csrc/k_step_u_sgf.cu",
             "csrc/k_step_q_sgf.cu", "csrc/k_step_a_sgf.cu", "csrc/k_step_p_sgf.cu",
-            "csrc/k_batch.cu", "csrc/k_batch_all.cu"]
+            "csrc/k_step_u_grid.cu", "csrc/k_step_q_grid.cu", "csrc/k_step_a_grid.cu",
+            "csrc/k_step_p_grid.cu", "csrc/k_batch.cu", "csrc/k_batch_all.cu"]
 _DEPS = _SOURCES + ["csrc/mppi_device.cuh", "csrc/mppi_tile.cuh", "csrc/kernels.cuh"]
 HEADER = os.path.join(_ROOT, "include", "dbasmppi.h")
 
@@ -127,6 +128,8 @@ def load():
     lib.mppi_create.argtypes = [C.POINTER(Params), _dp, C.POINTER(vp)]
     lib.mppi_create_tiled.argtypes = [C.POINTER(Params), _dp, C.POINTER(Tiling), C.POINTER(vp)]
     lib.mppi_set_obstacles.argtypes = [vp, _dp, C.c_int32]
+    lib.mppi_set_grid.argtypes = [vp, C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_double,
+                                  C.c_double, C.c_double]
     lib.mppi_step.argtypes = [vp, _dp, _dp, vp]
     lib.mppi_step_device.argtypes = [vp, vp, vp, vp]
     lib.mppi_get_control.argtypes = [vp, _dp, _dp]
@@ -288,6 +291,18 @@ class Controller:
     def set_obstacles(self, obstacles):
         ob = _f64(obstacles).reshape(-1, 3)
         _check(load().mppi_set_obstacles(self.h, _ptr(ob) if ob.size else None, ob.shape[0]))
+
+    def set_grid(self, sdf, ox: float = 0.0, oy: float = 0.0, res: float = 1.0):
+        """Set the grid map (ny x nx signed distances, sample (i, j) at
+        (ox + i res, oy + j res)), or remove it with sdf=None."""
+        if sdf is None:
+            _check(load().mppi_set_grid(self.h, None, 0, 0, 0.0, 0.0, 0.0))
+            return
+        g = np.ascontiguousarray(sdf, dtype=np.float32)
+        if g.ndim != 2:
+            raise ValueError("grid must be a 2-D array (ny x nx)")
+        _check(load().mppi_set_grid(self.h, g.ctypes.data_as(C.POINTER(C.c_float)), g.shape[1],
+                                    g.shape[0], float(ox), float(oy), float(res)))
 
     def step(self, x0, xref=None, stream=None):
         self._x0b[:] = x0

@@ -88,14 +88,18 @@ StepFn pick_kernel(int model, int npos, bool r80) {
   return table[model][npos == 14 ? 1 : 0][r80 ? 1 : 0];
 }
 
-// Step kernels that smooth the update (Savitzky-Golay, 96-register form):
-// separate instantiations, so the kernels above carry no trace of it.
-StepFn pick_sgf_kernel(int model, int npos) {
-  static const StepFn table[MPPI_NUM_MODELS][2] = {{step_u8_sgf, step_u14_sgf},
-                                                   {step_q8_sgf, step_q14_sgf},
-                                                   {step_a8_sgf, step_a14_sgf},
-                                                   {step_p8_sgf, step_p14_sgf}};
-  return table[model][npos == 14 ? 1 : 0];
+// Forms of the step kernels beyond the plain one (96-register form, separate
+// instantiations, so the plain kernels carry no trace of them): kFormSgf
+// smooths the update (Savitzky-Golay), kFormGrid adds the grid map's barrier
+// terms and smooths when asked.
+constexpr int kFormPlain = 0, kFormSgf = 1, kFormGrid = 2;
+StepFn pick_form_kernel(int form, int model, int npos) {
+  static const StepFn table[2][MPPI_NUM_MODELS][2] = {
+      {{step_u8_sgf, step_u14_sgf}, {step_q8_sgf, step_q14_sgf},
+       {step_a8_sgf, step_a14_sgf}, {step_p8_sgf, step_p14_sgf}},
+      {{step_u8_grid, step_u14_grid}, {step_q8_grid, step_q14_grid},
+       {step_a8_grid, step_a14_grid}, {step_p8_grid, step_p14_grid}}};
+  return table[form == kFormGrid ? 1 : 0][model][npos == 14 ? 1 : 0];
 }
 
 // World points a barrier thread holds: whole units of P points each; the
@@ -244,24 +248,25 @@ struct PickMemo {
 };
 std::mutex g_pick_mu;
 bool g_step_attr[kMaxPickDevices][MPPI_NUM_MODELS] = {};
-bool g_sgf_attr[kMaxPickDevices][MPPI_NUM_MODELS] = {};
+bool g_form_attr[kMaxPickDevices][2][MPPI_NUM_MODELS] = {};
 PickMemo g_pick_memo[kMaxPickDevices] = {};
 
-int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, bool sgf,
+int choose_step_kernel(int model, int npos, int threads, int smem, int nTiles, int form,
                        StepFn* out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxPickDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_pick_mu);
-  if (sgf) {
-    if (!g_sgf_attr[dev][model]) {
+  if (form != kFormPlain) {
+    bool& done = g_form_attr[dev][form == kFormGrid ? 1 : 0][model];
+    if (!done) {
       const int lim = max_smem_optin();
       for (int np : {8, 14})
-        CK(cudaFuncSetAttribute(pick_sgf_kernel(model, np),
+        CK(cudaFuncSetAttribute(pick_form_kernel(form, model, np),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-      g_sgf_attr[dev][model] = true;
+      done = true;
     }
-    *out = pick_sgf_kernel(model, npos);
+    *out = pick_form_kernel(form, model, npos);
     return MPPI_OK;
   }
   // only this model's kernels: with lazy module loading, touching a kernel
@@ -306,6 +311,7 @@ struct mppi_ctx {
   float2* d_cU = nullptr;
   float2* d_cA = nullptr;
   float* d_cw = nullptr;   // cw, then the smoothing weights when the update is smoothed
+  float* d_grid = nullptr; // the grid map, when one is set
   DevState* d_st = nullptr;
   double* d_obst = nullptr;
   double* d_in = nullptr;  // x0 (n) then xref ((T+1) n)
@@ -339,6 +345,13 @@ struct mppi_ctx {
 
 namespace {
 
+// The form of step kernel a context needs: the grid map's when it has one,
+// else the smoothing form when it smooths, else the plain one.
+int step_form(const mppi_ctx* c) {
+  if (c->d_grid) return kFormGrid;
+  return c->p.sgf_window > 0 ? kFormSgf : kFormPlain;
+}
+
 void free_ctx(mppi_ctx* c) {
   if (!c) return;
   if (c->last) cudaStreamSynchronize(c->last);
@@ -346,6 +359,7 @@ void free_ctx(mppi_ctx* c) {
   cudaFree(c->d_cU);
   cudaFree(c->d_cA);
   cudaFree(c->d_cw);
+  cudaFree(c->d_grid);
   cudaFree(c->d_st);
   cudaFree(c->d_obst);
   cudaFree(c->d_in);
@@ -594,7 +608,7 @@ int mppi_create_tiled(const mppi_params* p, const double* u_init, const mppi_til
   c->last = c->own;
   fill_desc(c);
   rc = choose_step_kernel(p->model, c->tl.positions_per_thread, c->tl.threads, c->smem, nTiles,
-                          p->sgf_window > 0,
+                          p->sgf_window > 0 ? kFormSgf : kFormPlain,
                           &c->fn);
   if (rc) {
     free_ctx(c);
@@ -658,13 +672,68 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
     return fail(MPPI_EINVAL, "obstacle set too large for the controller's tile shape");
   StepFn fn = nullptr;
   rc = choose_step_kernel(c->p.model, t.positions_per_thread, t.threads, smem, c->D.nTiles,
-                          c->p.sgf_window > 0, &fn);
+                          step_form(c), &fn);
   if (rc) return rc;
   c->tl = t;
   c->smem = smem;
   c->fn = fn;
   c->D.J = J;
   c->D.obst = c->d_obst;
+  return MPPI_OK;
+}
+
+int mppi_set_grid(mppi_ctx* c, const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
+                  double res) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  const bool off = nx == 0 && ny == 0;
+  if (!off) {
+    if (!sdf) return fail(MPPI_EINVAL, "grid pointer is NULL");
+    if (nx < 2 || ny < 2 || nx > MPPI_MAX_GRID_SIDE || ny > MPPI_MAX_GRID_SIDE ||
+        (int64_t)nx * ny > MPPI_MAX_GRID_SAMPLES)
+      return fail(MPPI_EINVAL, "grid of %d x %d samples: each side in [2, %d], at most %d samples",
+                  nx, ny, MPPI_MAX_GRID_SIDE, MPPI_MAX_GRID_SAMPLES);
+    if (!(res > 0) || !std::isfinite(res) || !std::isfinite(ox) || !std::isfinite(oy))
+      return fail(MPPI_EINVAL, "grid origin must be finite and its cell size finite and > 0");
+    for (size_t i = 0; i < (size_t)nx * ny; ++i)
+      if (!std::isfinite(sdf[i])) return fail(MPPI_EINVAL, "grid value %zu is not finite", i);
+  }
+  StepFn fn = nullptr;
+  int rc = choose_step_kernel(c->p.model, c->tl.positions_per_thread, c->tl.threads, c->smem,
+                              c->D.nTiles,
+                              off ? (c->p.sgf_window > 0 ? kFormSgf : kFormPlain) : kFormGrid, &fn);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->last));  // no step in flight reads the old map
+  float* nb = nullptr;
+  if (!off) {
+    const size_t bytes = sizeof(float) * (size_t)nx * ny;
+    if (cudaMalloc((void**)&nb, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPPI_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    if (cudaMemcpy(nb, sdf, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(nb);
+      return fail(MPPI_ECUDA, "grid upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+  }
+  // the map's fields of the device state (no kernel writes them)
+  DevState* hs = c->h_st;
+  hs->grid = nb;
+  hs->grid_nx = off ? 0 : nx;
+  hs->grid_ny = off ? 0 : ny;
+  hs->grid_ox = off ? 0.0 : ox;
+  hs->grid_oy = off ? 0.0 : oy;
+  hs->grid_res = off ? 0.0 : res;
+  hs->grid_inv_res = off ? 0.0f : (float)(1.0 / res);
+  hs->grid_pad = 0.0f;
+  const size_t o = offsetof(DevState, grid);
+  if (cudaMemcpy(reinterpret_cast<char*>(c->d_st) + o, reinterpret_cast<char*>(hs) + o,
+                 sizeof(DevState) - o, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(nb);
+    return fail(MPPI_ECUDA, "grid upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  cudaFree(c->d_grid);
+  c->d_grid = nb;
+  c->fn = fn;
   return MPPI_OK;
 }
 
@@ -947,7 +1016,7 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   const int nGroups = (nTiles + GT - 1) / GT;
   StepFn fn = nullptr;  // picked before anything is launched
   rc = choose_step_kernel(p->model, c.tl.positions_per_thread, c.tl.threads, c.smem, nTiles,
-                          p->sgf_window > 0, &fn);
+                          p->sgf_window > 0 ? kFormSgf : kFormPlain, &fn);
   if (rc) return rc;
   size_t off = 0;
   const size_t o_st = carve(&off, sizeof(DevState));

@@ -80,6 +80,25 @@ __global__ void step_p8_sgf(const __grid_constant__ CtrlDesc D, const double* __
 __global__ void step_p14_sgf(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
                              const double* __restrict__ xref);
 
+// The same with the grid map's terms compiled in (suffix _grid; smoothing
+// too), launched only for controllers that have a grid map.
+__global__ void step_u8_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_u14_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                              const double* __restrict__ xref);
+__global__ void step_q8_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_q14_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                              const double* __restrict__ xref);
+__global__ void step_a8_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_a14_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                              const double* __restrict__ xref);
+__global__ void step_p8_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                             const double* __restrict__ xref);
+__global__ void step_p14_grid(const __grid_constant__ CtrlDesc D, const double* __restrict__ x0,
+                              const double* __restrict__ xref);
+
 // Batched step: persistent CTAs pull (controller, tile) work items.
 struct WorkItem {
   int ctrl;  // index into the step table
@@ -104,7 +123,7 @@ __global__ void batch_kernel_all(const CtrlDesc* __restrict__ descs, unsigned ch
                                  double* __restrict__ u0_out);
 
 // Body of the one-controller step kernels.
-template <int MODEL, int NPOS, bool SGF = false>
+template <int MODEL, int NPOS, bool SGF = false, bool GRID = false>
 __device__ __forceinline__ void step_body(const CtrlDesc& D, const double* __restrict__ x0,
                                           const double* __restrict__ xref) {
   extern __shared__ __align__(16) char smem[];
@@ -112,7 +131,7 @@ __device__ __forceinline__ void step_body(const CtrlDesc& D, const double* __res
   if (threadIdx.x == 0) mbar_init(&ts.mbar);
   __syncthreads();
   uint32_t phase = 0u;
-  run_tile<MODEL, NPOS, false, SGF>(D, blockIdx.x, x0, xref, smem, ts, phase);
+  run_tile<MODEL, NPOS, false, SGF, GRID>(D, blockIdx.x, x0, xref, smem, ts, phase);
 }
 
 }  // namespace dbm

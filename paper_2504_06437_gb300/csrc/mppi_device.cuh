@@ -74,6 +74,13 @@ struct DevState {
   unsigned long long iter;  // Philox counter words 2..3
   int first;         // 1 until the first step
   int status;        // kStatus*
+  // grid map, set by the host (mppi_set_grid) and read by the grid form of
+  // the step kernels: signed distances (m), sample (i, j) at
+  // (grid_ox + i res, grid_oy + j res), stored at grid[j grid_nx + i]; or null
+  const float* grid;
+  int grid_nx, grid_ny;
+  double grid_ox, grid_oy, grid_res;
+  float grid_inv_res, grid_pad;
 };
 
 // Outputs of a step that the host reads after every step, written by the
@@ -417,6 +424,52 @@ struct TileScratch {
   unsigned long long iter;             // iteration counter of this step
 };
 
+// The grid map as a tile reads it.  The tile's frame is centred on the
+// measured position x0, whose grid coordinates are split (in FP64) into the
+// integer cell (ci, cj) and the remainder (ru, rv) in [0, 1): a point X of
+// the tile's frame has grid coordinate ci + (ru + X / res), and the FP32
+// part stays small, so its rounding is that of a few cells, not of the
+// whole map.
+struct GridView {
+  const float* g;
+  int nx, ny, ci, cj;
+  float ru, rv, inv_res;
+};
+
+// One axis of the lookup: cell index in [0, n - 2] and weight in [0, 1] of
+// grid coordinate c + l, with the coordinate clamped to [0, n - 1] first.
+// The first clamp bounds l to just beyond the map (fminf / fmaxf return the
+// number when the other operand is NaN), so the index is finite for any
+// input.
+__device__ __forceinline__ int grid_axis(int c, float l, int n, float& f) {
+  l = fminf(fmaxf(l, (float)(-1 - c)), (float)(n - c));
+  const float fl = floorf(l);
+  int i = c + (int)fl;
+  f = l - fl;
+  if (i < 0) {
+    i = 0;
+    f = 0.0f;
+  } else if (i >= n - 1) {
+    i = n - 2;
+    f = 1.0f;
+  }
+  return i;
+}
+
+// The grid map's h at a point of the tile's frame (Sec. V-C grid map):
+// bilinear interpolation of the four samples around it, the grid
+// coordinates first clamped to [0, nx - 1] x [0, ny - 1]; nx, ny >= 2.
+__device__ __forceinline__ float grid_h(const GridView& gv, float X, float Y) {
+  float fx, fy;
+  const int i = grid_axis(gv.ci, fmaf(X, gv.inv_res, gv.ru), gv.nx, fx);
+  const int j = grid_axis(gv.cj, fmaf(Y, gv.inv_res, gv.rv), gv.ny, fy);
+  const float* r0 = gv.g + (size_t)j * gv.nx + i;
+  const float* r1 = r0 + gv.nx;
+  const float g00 = __ldg(r0), g10 = __ldg(r0 + 1), g01 = __ldg(r1), g11 = __ldg(r1 + 1);
+  const float a = fmaf(fx, g10 - g00, g00), b = fmaf(fx, g11 - g01, g01);
+  return fmaf(fy, b - a, a);
+}
+
 // Fused barrier over nunits = T S (step, sample) units; unit u = t S + s has
 // its pose at pose[t SP + s] (SP = row_stride(S, BATCHED)) and P shape
 // points shp[0..P).  Each thread takes NPOS / P whole units at a
@@ -433,12 +486,14 @@ struct TileScratch {
 // points are summed exactly (TwoSum) into (hi, lo), stored at
 // uB[u * ustride]; the sign bit of hi marks a unit in which some h <= 0
 // (collision).  A thread reads the poses of its units before it writes their
-// sums, so uB may overlay pose.
-template <int NPOS, bool BATCHED>
+// sums, so uB may overlay pose.  GRID: each point also adds the grid map's
+// term (grid_h) and counts its h in the collision test.
+template <int NPOS, bool BATCHED, bool GRID = false>
 __device__ __forceinline__ void barrier_units(int nunits, int S, int P, int J, const float4* pose,
                                               const float2* __restrict__ shp,
                                               const float4* __restrict__ obs4, float h_eps,
-                                              float2* uB, int ustride, int tid, int nthreads) {
+                                              float2* uB, int ustride, int tid, int nthreads,
+                                              const GridView* gv = nullptr) {
   // unit u = t S + s lives at t SP + s = u + (SP - S) floor(u / S); the
   // quotient by one multiply-high with m = ceil(2^32 / S), exact while
   // u (m S - 2^32) < 2^32 (here u < T S <= 2^13 and m S - 2^32 < S <= 32)
@@ -517,6 +572,18 @@ __device__ __forceinline__ void barrier_units(int nunits, int S, int P, int J, c
         mn[2 * k + 1] = fminf(mn[2 * k + 1], h.y);
         acc2[k] = __fadd2_rn(acc2[k], make_float2(rcp_approx(fmaxf(h.x, h_eps)),
                                                   rcp_approx(fmaxf(h.y, h_eps))));
+      }
+    }
+    if constexpr (GRID) {
+      if (gv->g) {
+#pragma unroll
+        for (int k = 0; k < NP2; ++k) {
+          const float hx = grid_h(*gv, X2[k].x, Y2[k].x), hy = grid_h(*gv, X2[k].y, Y2[k].y);
+          mn[2 * k] = fminf(mn[2 * k], hx);
+          mn[2 * k + 1] = fminf(mn[2 * k + 1], hy);
+          acc2[k] = __fadd2_rn(acc2[k], make_float2(rcp_approx(fmaxf(hx, h_eps)),
+                                                    rcp_approx(fmaxf(hy, h_eps))));
+        }
       }
     }
     FF f = {0.0f, 0.0f};
@@ -679,11 +746,13 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
 // Fused barrier over npos positions, one position per thread at a time
 // (position i = unit i / P, shape point i % P): the fully parallel form used
 // for the single nominal trajectory.  out[i] = +-sum_j 1/max(h, h_eps), the
-// sign bit marking some h <= 0.
+// sign bit marking some h <= 0.  GRID: plus the grid map's term.
+template <bool GRID = false>
 __device__ __forceinline__ void barrier_flat(int npos, int P, int J, const float4* __restrict__ pose,
                                              const float2* __restrict__ shp,
                                              const float4* __restrict__ obs4, float h_eps,
-                                             float* __restrict__ out, int tid, int nthreads) {
+                                             float* __restrict__ out, int tid, int nthreads,
+                                             const GridView* gv = nullptr) {
   for (int i = tid; i < npos; i += nthreads) {
     const int u = i / P, p = i - u * P;
     const float4 ps = pose[u];
@@ -697,6 +766,13 @@ __device__ __forceinline__ void barrier_flat(int npos, int P, int J, const float
       float h = fmaf(dx, dx, fmaf(dy, dy, o.z));
       mn = fminf(mn, h);
       acc += rcp_approx(fmaxf(h, h_eps));
+    }
+    if constexpr (GRID) {
+      if (gv->g) {
+        const float h = grid_h(*gv, X, Y);
+        mn = fminf(mn, h);
+        acc += rcp_approx(fmaxf(h, h_eps));
+      }
     }
     out[i] = mn <= 0.0f ? -acc : acc;
   }

@@ -385,6 +385,29 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // Sigma^-1 u_t and sum_t u_t . a'_t) are formed in the same pass as U* and
 // the shift, one step per thread; S_e enters afterwards through L, C0 and
 // the 1 / S_e that the next step applies to a'_t.
+// The grid map in the tile's frame, whose origin is the measured position
+// (x0g[0], x0g[1]); built where it is used rather than held in registers
+// across the tile.
+__device__ __forceinline__ GridView grid_view(const CtrlDesc& D, const double* __restrict__ x0g) {
+  const DevState* st = D.st;
+  GridView gv;
+  gv.g = st->grid;
+  gv.nx = st->grid_nx;
+  gv.ny = st->grid_ny;
+  gv.inv_res = st->grid_inv_res;
+  if (!gv.g) return gv;
+  // x0's grid coordinates, bounded so that the cell fits an int (beyond the
+  // bound every point lies off the map and clamps to its edge anyway)
+  const double u = fmin(fmax((x0g[0] - st->grid_ox) / st->grid_res, -1073741824.0), 1073741824.0);
+  const double v = fmin(fmax((x0g[1] - st->grid_oy) / st->grid_res, -1073741824.0), 1073741824.0);
+  const double fu = floor(u), fv = floor(v);
+  gv.ci = (int)fu;
+  gv.cj = (int)fv;
+  gv.ru = (float)(u - fu);
+  gv.rv = (float)(v - fv);
+  return gv;
+}
+
 // Algorithm 1's SGF on the merged column sums, in place: hi[2t + d] becomes
 // the smoothed sum and lo[2t + d] zero.  The filter is linear, so smoothing
 // the sums before their common 1 / Z scale is smoothing the update.  Window
@@ -409,9 +432,10 @@ __device__ __forceinline__ void sgf_columns(const float* __restrict__ w, int W, 
   __syncthreads();
 }
 
-template <int MODEL, int NPOS>
+template <int MODEL, int NPOS, bool GRID = false>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
-                            const double* __restrict__ x0g, double* out) {
+                            const double* __restrict__ x0g, double* out,
+                            const GridView* gv = nullptr) {
   const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int T = D.T, P = D.P;
   const double* Us = reinterpret_cast<const double*>(smem + L.Us);  // the step's U
@@ -468,7 +492,7 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
                                   lane, x1);
   }
   __syncthreads();
-  barrier_flat(T * P, P, D.J, pose_nom, shp, obs4, D.h_eps, b_nom, tid, nthreads);
+  barrier_flat<GRID>(T * P, P, D.J, pose_nom, shp, obs4, D.h_eps, b_nom, tid, nthreads, gv);
   __syncthreads();
   if (tid < 32) {
     FF a = {0.0f, 0.0f};
@@ -529,11 +553,12 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 // one-batch form of merge_partials and the odd row stride of row_stride;
 // the one-controller kernels take the pipelined merge and SP = S.  Both
 // choices were measured per kernel; the results are the same bit for bit.
+// GRID: the grid map's terms are compiled in (taken when D.st->grid is set).
 // SGF: the Savitzky-Golay pass is compiled in (taken when D.sgf_wp is set).
 // The batch kernels carry it, and the one-controller kernels have a form
 // with it and one without, so that controllers that do not smooth run code
 // with no trace of it.
-template <int MODEL, int NPOS, bool BATCHED, bool SGF = BATCHED>
+template <int MODEL, int NPOS, bool BATCHED, bool SGF = BATCHED, bool GRID = false>
 __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
                          const double* __restrict__ xrefg, char* smem, TileScratch& ts,
                          uint32_t& mbar_phase, double* u0_out = nullptr) {
@@ -640,6 +665,18 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   sincosf((float)D.x_goal[2], &gs, &gc);
   sincosf((float)x0g[2], &xs, &xc);
   float bd = 0.0f, b0 = 0.0f;
+  if constexpr (GRID) {
+    const GridView gv = grid_view(D, x0g);
+    if (gv.g) {
+      for (int p = tid; p < P; p += nthreads) {
+        const float2 sh = shp[p];
+        bd += 1.0f / fmaxf(grid_h(gv, fmaf(gc, sh.x, fmaf(-gs, sh.y, gx)),
+                                  fmaf(gs, sh.x, fmaf(gc, sh.y, gy))), D.h_eps);
+        b0 += 1.0f / fmaxf(grid_h(gv, fmaf(xc, sh.x, -xs * sh.y), fmaf(xs, sh.x, xc * sh.y)),
+                           D.h_eps);
+      }
+    }
+  }
   for (int i = tid; i < P * J; i += nthreads) {
     int p = i / J, j = i - p * J;
     float2 sh = shp[p];
@@ -717,7 +754,13 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   __syncthreads();
 
   // ---- fused barrier over all (step, sample) units, sums over the poses
-  barrier_units<NPOS, BATCHED>(T * S, S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid, nthreads);
+  if constexpr (GRID) {
+    const GridView gv = grid_view(D, x0g);
+    barrier_units<NPOS, BATCHED, true>(T * S, S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid,
+                                       nthreads, &gv);
+  } else {
+    barrier_units<NPOS, BATCHED>(T * S, S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid, nthreads);
+  }
   __syncthreads();
 
   // ---- barrier-state and collision costs: one warp per sample; costs are
@@ -837,7 +880,12 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
                   reinterpret_cast<float*>(smem + L.region), tid, nthreads);
   }
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
-  final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
+  if constexpr (GRID) {
+    const GridView gv = grid_view(D, x0g);
+    final_stage<MODEL, NPOS, true>(D, smem, L, ts, x0g, u0_out, &gv);
+  } else {
+    final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
+  }
 }
 
 }  // namespace dbm

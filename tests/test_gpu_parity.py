@@ -65,6 +65,8 @@ def run_pair(gpu, orc, world, steps=1, tiling=None, u_init=None):
     errs = []
     with gpu.Controller(p, u_init=u_init, tiling=tiling) as g:
         g.set_obstacles(world.obstacles)
+        if p.get("grid") is not None:
+            g.set_grid(p["grid"], p["grid_ox"], p["grid_oy"], p["grid_res"])
         x = world.x_start.copy()
         for i in range(steps):
             if i > 0:
@@ -393,3 +395,88 @@ def test_sgf_rejects_bad_parameters(gpu, window, order):
     with pytest.raises(gpu.MppiError) as e:
         gpu.Controller(w.params)
     assert e.value.code == gpu.MPPI_EINVAL
+
+
+# ------------------------------------------------ grid map (Sec. V-C)
+
+def test_grid_mission_closed_loop(gpu, orc):
+    """The vehicle mission with its obstacles as a 1001 x 301 signed-distance
+    grid (no circles): three receding-horizon steps, every sample's cost,
+    the collided set and U* against the oracle's bilinear lookups."""
+    run_pair(gpu, orc, W.ackermann_grid(0), steps=3)
+
+
+@pytest.mark.parametrize("tiling", [dict(samples_per_cta=13, threads=128, positions_per_thread=8),
+                                    dict(samples_per_cta=9, threads=256, positions_per_thread=14)])
+def test_grid_ragged_tiles(gpu, orc, tiling):
+    """Ragged last tile (K 777) and both point counts per barrier thread."""
+    run_pair(gpu, orc, W.ackermann_grid(1, K=777, T=23), steps=1, tiling=tiling)
+
+
+def test_grid_with_circles_and_smoothing(gpu, orc):
+    """Grid map and circle obstacles together (their terms add), with the
+    update smoothed, on the 6-state quadrotor: the grid form of the kernel
+    carries both passes."""
+    w = W.quad2d(3, K=2048, T=40)
+    lo = w.obstacles[:, :2].min(axis=0) - 3.0
+    g = W.sdf_grid(w.obstacles[::3], [], lo[0], lo[1], 0.05, 400, 300)
+    p = dict(w.params, grid=g, grid_ox=float(lo[0]), grid_oy=float(lo[1]), grid_res=0.05,
+             sgf_window=7, sgf_order=2)
+    run_pair(gpu, orc, dataclasses.replace(w, params=p), steps=2)
+
+
+def test_grid_collisions(gpu, orc):
+    """A wall 0.2 m ahead of the vehicle's front at 0.5 m/s: about 600 of the
+    1024 samples reach h <= 0 on the grid; the collided set and the
+    collision costs match the oracle."""
+    w = W.ackermann(2, K=1024, T=20)
+    xs = w.x_start.copy()
+    xs[3] = 0.5
+    g = W.sdf_grid([], [(7.2, 10.0, 8.0, 20.0)], 0.0, 5.0, 0.02, 600, 600)
+    p = dict(w.params, grid=g, grid_ox=0.0, grid_oy=5.0, grid_res=0.02)
+    world = dataclasses.replace(w, params=p, obstacles=np.zeros((0, 3)), x_start=xs)
+    ctl = orc.new_controller(p)
+    xref = world.reference(world.x_start)
+    ro = orc.step(p, world.obstacles, world.x_start, xref, ctl)
+    assert 50 < int(ro["coll"].sum()) < 1000
+    run_pair(gpu, orc, world, steps=2)
+
+
+def test_grid_removed_is_plain_kernel_bit_for_bit(gpu):
+    """Setting a map and removing it again leaves a controller whose steps
+    equal, bit for bit, those of a controller that never had one."""
+    w = W.ackermann(3)
+    g = W.ackermann_grid(3).params["grid"]
+    with gpu.Controller(w.params) as a, gpu.Controller(w.params) as b:
+        a.set_obstacles(w.obstacles)
+        b.set_obstacles(w.obstacles)
+        a.set_grid(g, 0.0, 0.0, 0.1)
+        a.step(w.x_start, w.reference(w.x_start))
+        a.get_control()
+        a.set_grid(None)
+        b.step(w.x_start, w.reference(w.x_start))
+        b.get_control()
+        st = b.get_state()
+        a.set_state(st["U"], st["S_e"], st["beta"], st["first"], st["iter"])
+        for _ in range(2):
+            a.step(w.x_start, w.reference(w.x_start))
+            b.step(w.x_start, w.reference(w.x_start))
+        ua, Ua = a.get_control(want_U=True)
+        ub, Ub = b.get_control(want_U=True)
+        np.testing.assert_array_equal(ua, ub)
+        np.testing.assert_array_equal(Ua, Ub)
+        np.testing.assert_array_equal(a.get_debug()["costs"], b.get_debug()["costs"])
+
+
+def test_grid_rejects_bad_maps(gpu):
+    w = W.ackermann(0)
+    with gpu.Controller(w.params) as c:
+        good = np.zeros((4, 5), dtype=np.float32)
+        for args in [(np.zeros((1, 5)), 0.0, 0.0, 0.1), (np.zeros((4, 1)), 0.0, 0.0, 0.1),
+                     (good, 0.0, 0.0, 0.0), (good, 0.0, 0.0, -1.0), (good, np.nan, 0.0, 0.1),
+                     (np.full((4, 5), np.inf), 0.0, 0.0, 0.1)]:
+            with pytest.raises(gpu.MppiError) as e:
+                c.set_grid(*args)
+            assert e.value.code == gpu.MPPI_EINVAL
+        c.set_grid(good, 0.0, 0.0, 0.1)
+        c.set_grid(None)
