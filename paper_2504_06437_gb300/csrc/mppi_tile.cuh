@@ -386,8 +386,8 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // the shift, one step per thread; S_e enters afterwards through L, C0 and
 // the 1 / S_e that the next step applies to a'_t.
 // The grid map in the tile's frame, whose origin is the measured position
-// (x0g[0], x0g[1]); built where it is used rather than held in registers
-// across the tile.
+// (x0g[0], x0g[1]).  FP64, so one thread builds it (grid_shared) and the
+// others read it from shared memory.
 __device__ __forceinline__ GridView grid_view(const CtrlDesc& D, const double* __restrict__ x0g) {
   const DevState* st = D.st;
   GridView gv;
@@ -406,6 +406,12 @@ __device__ __forceinline__ GridView grid_view(const CtrlDesc& D, const double* _
   gv.ru = (float)(u - fu);
   gv.rv = (float)(v - fv);
   return gv;
+}
+
+// The CTA's copy of its grid view (only the grid kernels instantiate it).
+__device__ __forceinline__ GridView& grid_shared() {
+  __shared__ GridView s;
+  return s;
 }
 
 // Algorithm 1's SGF on the merged column sums, in place: hi[2t + d] becomes
@@ -639,6 +645,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   if (tid == 0) {  // read early: only the final stage uses them
     ts.S_e_used = S_e;
     ts.iter = iter;
+    if constexpr (GRID) grid_shared() = grid_view(D, x0g);  // read after the next barrier
   }
   if (J > 0) {
 #if DBM_STAGE_TMA
@@ -666,7 +673,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   sincosf((float)x0g[2], &xs, &xc);
   float bd = 0.0f, b0 = 0.0f;
   if constexpr (GRID) {
-    const GridView gv = grid_view(D, x0g);
+    const GridView gv = grid_shared();
     if (gv.g) {
       for (int p = tid; p < P; p += nthreads) {
         const float2 sh = shp[p];
@@ -755,7 +762,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
 
   // ---- fused barrier over all (step, sample) units, sums over the poses
   if constexpr (GRID) {
-    const GridView gv = grid_view(D, x0g);
+    const GridView gv = grid_shared();
     barrier_units<NPOS, BATCHED, true>(T * S, S, P, J, pose, shp, obs4, D.h_eps, uB, 2, tid,
                                        nthreads, &gv);
   } else {
@@ -881,7 +888,7 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   }
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
   if constexpr (GRID) {
-    const GridView gv = grid_view(D, x0g);
+    const GridView gv = grid_shared();
     final_stage<MODEL, NPOS, true>(D, smem, L, ts, x0g, u0_out, &gv);
   } else {
     final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
