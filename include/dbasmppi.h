@@ -214,6 +214,14 @@ int mppi_io_bytes(mppi_ctx* c, uint64_t* h2d, uint64_t* d2h);
 int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J,
                   int32_t iters, mppi_tiling* best, float* best_us);
 
+/* The same for a controller with a grid map (arguments as mppi_set_grid;
+ * sdf NULL = no map, as mppi_autotune): the candidates run the grid form of
+ * the step kernel.  Errors: as mppi_autotune, and mppi_set_grid's for the
+ * map. */
+int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int32_t J, const float* sdf,
+                       int32_t nx, int32_t ny, double ox, double oy, double res, int32_t iters,
+                       mppi_tiling* best, float* best_us);
+
 /* The launch shape in use and the number of CTAs of one step. */
 int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas);
 

@@ -143,6 +143,9 @@ def load():
     lib.mppi_debug_draws.argtypes = [C.POINTER(Params), C.c_double, C.c_uint64, C.c_int32,
                                      C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     lib.mppi_debug_wait_probe.argtypes = [C.c_int64, C.c_int32]
+    lib.mppi_autotune_grid.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.POINTER(C.c_float),
+                                       C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                       C.c_int32, C.POINTER(Tiling), C.POINTER(C.c_float)]
     lib.mppi_autotune.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.c_int32,
                                   C.POINTER(Tiling), C.POINTER(C.c_float)]
     lib.mppi_batch_create.argtypes = [C.c_int32, C.c_size_t, C.POINTER(vp)]
@@ -230,13 +233,23 @@ def debug_draws(cfg: dict, S_e: float, it: int, K: int, T: int):
 
 
 def autotune(cfg: dict, obstacles, iters: int = 10):
-    """Fastest launch shape for this problem: (tiling dict, microseconds per step)."""
+    """Fastest launch shape for this problem: (tiling dict, microseconds per step).
+    A grid map in cfg (``grid``, ``grid_ox``, ``grid_oy``, ``grid_res``) is
+    set on every candidate."""
     p = make_params(cfg)
     ob = _f64(obstacles).reshape(-1, 3)
     t = Tiling()
     us = C.c_float()
-    _check(load().mppi_autotune(C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0], int(iters),
-                                C.byref(t), C.byref(us)))
+    g = cfg.get("grid")
+    if g is not None:
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        _check(load().mppi_autotune_grid(
+            C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0],
+            g.ctypes.data_as(C.POINTER(C.c_float)), g.shape[1], g.shape[0], float(cfg["grid_ox"]),
+            float(cfg["grid_oy"]), float(cfg["grid_res"]), int(iters), C.byref(t), C.byref(us)))
+    else:
+        _check(load().mppi_autotune(C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0],
+                                    int(iters), C.byref(t), C.byref(us)))
     return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
                 positions_per_thread=t.positions_per_thread, chunk_steps=0), float(us.value)
 

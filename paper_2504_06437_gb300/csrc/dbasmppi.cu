@@ -682,20 +682,27 @@ int mppi_set_obstacles(mppi_ctx* c, const double* cxcyr, int32_t J) {
   return MPPI_OK;
 }
 
+namespace {
+int check_grid(const float* sdf, int32_t nx, int32_t ny, double ox, double oy, double res) {
+  if (!sdf) return fail(MPPI_EINVAL, "grid pointer is NULL");
+  if (nx < 2 || ny < 2 || nx > MPPI_MAX_GRID_SIDE || ny > MPPI_MAX_GRID_SIDE ||
+      (int64_t)nx * ny > MPPI_MAX_GRID_SAMPLES)
+    return fail(MPPI_EINVAL, "grid of %d x %d samples: each side in [2, %d], at most %d samples",
+                nx, ny, MPPI_MAX_GRID_SIDE, MPPI_MAX_GRID_SAMPLES);
+  if (!(res > 0) || !std::isfinite(res) || !std::isfinite(ox) || !std::isfinite(oy))
+    return fail(MPPI_EINVAL, "grid origin must be finite and its cell size finite and > 0");
+  for (size_t i = 0; i < (size_t)nx * ny; ++i)
+    if (!std::isfinite(sdf[i])) return fail(MPPI_EINVAL, "grid value %zu is not finite", i);
+  return MPPI_OK;
+}
+}  // namespace
+
 int mppi_set_grid(mppi_ctx* c, const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
                   double res) {
   if (!c) return fail(MPPI_ESTATE, "context is NULL");
   const bool off = nx == 0 && ny == 0;
   if (!off) {
-    if (!sdf) return fail(MPPI_EINVAL, "grid pointer is NULL");
-    if (nx < 2 || ny < 2 || nx > MPPI_MAX_GRID_SIDE || ny > MPPI_MAX_GRID_SIDE ||
-        (int64_t)nx * ny > MPPI_MAX_GRID_SAMPLES)
-      return fail(MPPI_EINVAL, "grid of %d x %d samples: each side in [2, %d], at most %d samples",
-                  nx, ny, MPPI_MAX_GRID_SIDE, MPPI_MAX_GRID_SAMPLES);
-    if (!(res > 0) || !std::isfinite(res) || !std::isfinite(ox) || !std::isfinite(oy))
-      return fail(MPPI_EINVAL, "grid origin must be finite and its cell size finite and > 0");
-    for (size_t i = 0; i < (size_t)nx * ny; ++i)
-      if (!std::isfinite(sdf[i])) return fail(MPPI_EINVAL, "grid value %zu is not finite", i);
+    if (int rc = check_grid(sdf, nx, ny, ox, oy, res)) return rc;
   }
   StepFn fn = nullptr;
   int rc = choose_step_kernel(c->p.model, c->tl.positions_per_thread, c->tl.threads, c->smem,
@@ -1081,8 +1088,15 @@ constexpr int kTuneMaxReps = 400;
 
 extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J, int32_t iters,
                              mppi_tiling* best, float* best_us) {
+  return mppi_autotune_grid(p, cxcyr, J, nullptr, 0, 0, 0.0, 0.0, 0.0, iters, best, best_us);
+}
+
+extern "C" int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int32_t J,
+                                  const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
+                                  double res, int32_t iters, mppi_tiling* best, float* best_us) {
   int rc = validate(p);
   if (rc) return rc;
+  if (sdf && (rc = check_grid(sdf, nx, ny, ox, oy, res))) return rc;
   if (!best) return fail(MPPI_EINVAL, "best is NULL");
   if (iters < 1) iters = 5;
   const int sms = num_sms();
@@ -1110,7 +1124,8 @@ extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t 
         mppi_tiling t = {S, NT, NP, 0};
         mppi_ctx* c = nullptr;
         if (mppi_create_tiled(p, nullptr, &t, &c) != MPPI_OK) continue;
-        if (mppi_set_obstacles(c, cxcyr, J) != MPPI_OK || c->tl.samples_per_cta != S) {
+        if (mppi_set_obstacles(c, cxcyr, J) != MPPI_OK || c->tl.samples_per_cta != S ||
+            (sdf && mppi_set_grid(c, sdf, nx, ny, ox, oy, res) != MPPI_OK)) {
           mppi_destroy(c);
           continue;
         }

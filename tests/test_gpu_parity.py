@@ -480,3 +480,13 @@ def test_grid_rejects_bad_maps(gpu):
             assert e.value.code == gpu.MPPI_EINVAL
         c.set_grid(good, 0.0, 0.0, 0.1)
         c.set_grid(None)
+
+
+def test_grid_autotune(gpu, orc):
+    """The grid-aware autotuner runs the grid form of the kernel on every
+    candidate and returns a launch shape under which the step matches the
+    oracle."""
+    w = W.ackermann_grid(2, K=512, T=20)
+    tiling, us = gpu.autotune(w.params, w.obstacles, iters=3)
+    assert us > 0 and tiling["threads"] in (128, 256, 512)
+    run_pair(gpu, orc, w, steps=1, tiling=tiling)
