@@ -490,3 +490,18 @@ def test_grid_autotune(gpu, orc):
     tiling, us = gpu.autotune(w.params, w.obstacles, iters=3)
     assert us > 0 and tiling["threads"] in (128, 256, 512)
     run_pair(gpu, orc, w, steps=1, tiling=tiling)
+
+
+@pytest.mark.parametrize("name", ["unicycle_small", "quad5"])
+def test_grid_other_models(gpu, orc, name):
+    """The grid form on the unicycle and the 5-state quadrotor: each world's
+    circles rasterised into a signed-distance grid (no circles passed), two
+    receding-horizon steps against the oracle."""
+    w = W.PRESETS[name](5)
+    lo = w.obstacles[:, :2].min(axis=0) - 2.0
+    hi = w.obstacles[:, :2].max(axis=0) + 2.0
+    res = 0.05
+    nx, ny = int((hi[0] - lo[0]) / res) + 2, int((hi[1] - lo[1]) / res) + 2
+    g = W.sdf_grid(w.obstacles, [], lo[0], lo[1], res, nx, ny)
+    p = dict(w.params, grid=g, grid_ox=float(lo[0]), grid_oy=float(lo[1]), grid_res=res)
+    run_pair(gpu, orc, dataclasses.replace(w, params=p, obstacles=np.zeros((0, 3))), steps=2)
