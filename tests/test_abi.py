@@ -84,6 +84,10 @@ def _bad(cfg_over):
     dict(sigma=[1.0, 0.5, 0.2, 1.0]), dict(sigma=[-1.0, 0.0, 0.0, 1.0]),
     dict(sigma=[0.0, 0.0, 0.0, 0.0]), dict(u_min=[1.0, 0.0], u_max=[0.0, 1.0]),
     dict(dt=float("nan")), dict(ln_sigma=-0.1), dict(n_shape=9), dict(n_shape=0),
+    # Savitzky-Golay smoothing: even, too wide for T = 10, order >= window, order > 6
+    dict(sgf_window=4, sgf_order=1), dict(sgf_window=11, sgf_order=2),
+    dict(sgf_window=5, sgf_order=5), dict(sgf_window=9, sgf_order=7),
+    dict(sgf_window=-3, sgf_order=0), dict(sgf_window=1, sgf_order=0),
 ])
 def test_create_rejects_bad_params_without_gpu(lib, over):
     p = binding.make_params(_bad(over))
@@ -96,8 +100,26 @@ def test_create_rejects_bad_params_without_gpu(lib, over):
     assert not h.value
 
 
+@pytest.mark.parametrize("nx,ny,res,value", [(1, 5, 0.1, 0.0), (5, 1, 0.1, 0.0), (4, 4, 0.0, 0.0),
+                                             (4, 4, -0.5, 0.0), (4, 4, float("inf"), 0.0),
+                                             (4, 4, 0.1, float("nan")), (70000, 2, 0.1, 0.0)])
+def test_grid_rejected_without_gpu(lib, nx, ny, res, value):
+    """The grid map's checks (sides, cell size, finite samples) run before
+    any CUDA call: mppi_autotune_grid refuses a bad map on a host without a
+    GPU."""
+    p = binding.make_params(_bad({}))
+    g = np.full((ny, nx), value, dtype=np.float32)
+    t = binding.Tiling()
+    us = C.c_float()
+    rc = lib.mppi_autotune_grid(C.byref(p), None, 0, g.ctypes.data_as(C.POINTER(C.c_float)), nx, ny,
+                                0.0, 0.0, res, 1, C.byref(t), C.byref(us))
+    assert rc == binding.MPPI_EINVAL
+    assert b"grid" in lib.mppi_last_error()
+
+
 def test_null_handles(lib):
     assert lib.mppi_destroy(None) == binding.MPPI_OK
     assert lib.mppi_step(None, None, None, None) == binding.MPPI_ESTATE
     assert lib.mppi_get_control(None, None, None) == binding.MPPI_ESTATE
     assert lib.mppi_set_obstacles(None, None, 0) == binding.MPPI_ESTATE
+    assert lib.mppi_set_grid(None, None, 0, 0, 0.0, 0.0, 0.0) == binding.MPPI_ESTATE
