@@ -183,9 +183,13 @@ int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref,
 
 /* After a step: u0 = u*_0 (2 doubles, the control to apply) and, if U is
  * not NULL, the shifted nominal sequence for the next step (T x 2).
- * Synchronises with the context's last stream.  u0 and the status word are
- * written by the step itself into mapped pinned host memory, so only U, when
- * asked for, is copied.  Errors: MPPI_ESTATE (no step has run),
+ * u0 and the status word are written by the step itself into mapped pinned
+ * host memory, followed (after a system-scope fence) by the step's
+ * iteration number.  With U NULL the call returns as soon as that number
+ * shows the last enqueued step, which can be before its kernel has retired;
+ * the stream keeps the order of later work.  If the stream ends without it
+ * (an error), or when U is asked for, it synchronises with the context's
+ * last stream (U is then copied).  Errors: MPPI_ESTATE (no step has run),
  * MPPI_ETIMEOUT (a bounded device wait of the step expired), MPPI_ECUDA. */
 int mppi_get_control(mppi_ctx* c, double* u0, double* U);
 

@@ -341,6 +341,7 @@ struct mppi_ctx {
   cudaStream_t own = nullptr;
   cudaStream_t last = nullptr;
   bool stepped = false;
+  uint64_t iter = 0;  // iteration counter of the device state after the steps enqueued so far
 };
 
 namespace {
@@ -752,6 +753,7 @@ int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref, void
   CK(cudaGetLastError());
   c->last = s;
   c->stepped = true;
+  ++c->iter;
   return MPPI_OK;
 }
 
@@ -784,6 +786,29 @@ int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
   if (!c->stepped) return fail(MPPI_ESTATE, "no step has run");
   // u0 and the status word come from the mapped mirror the step's final
   // stage wrote; only U, when asked for, is copied
+  if (!U) {
+    // the last step's final stage stores seq after its u0 and status (and a
+    // system-scope fence): once seq shows that step, the mirror holds its
+    // output, without waiting for the kernel to retire.  The stream is
+    // polled now and then, so a step that ended without writing (an error)
+    // falls through to the synchronisation below, which reports it.
+    const int want = (int)(uint32_t)c->iter;
+    volatile int* seq = &c->h_out->seq;
+    for (unsigned n = 1;; ++n) {
+      if (*seq == want) {
+        std::atomic_thread_fence(std::memory_order_acquire);
+        const volatile HostOut* o = c->h_out;
+        if (o->status == kStatusTimeout)
+          return fail(MPPI_ETIMEOUT, "a bounded device wait (obstacle staging) expired");
+        if (u0) {
+          u0[0] = o->u0[0];
+          u0[1] = o->u0[1];
+        }
+        return MPPI_OK;
+      }
+      if ((n & 1023u) == 0u && cudaStreamQuery(c->last) != cudaErrorNotReady) break;
+    }
+  }
   if (U) CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost, c->last));
   CK(cudaStreamSynchronize(c->last));
   if (c->h_out->status == kStatusTimeout)
@@ -875,6 +900,7 @@ int mppi_set_state(mppi_ctx* c, const double* U, double S_e, double beta, int32_
   st.first = first ? 1 : 0;
   st.iter = iter;
   st.status = 0;
+  c->iter = iter;
   CK(cudaMemcpy(c->d_U, U, sizeof(double) * 2 * c->p.T, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->d_st, &st, sizeof(DevState), cudaMemcpyHostToDevice));
   prep_kernel<<<1, 256, 0, c->own>>>(c->D, 0);

@@ -85,11 +85,12 @@ struct DevState {
 
 // Outputs of a step that the host reads after every step, written by the
 // final stage straight into mapped pinned host memory (one-controller
-// contexts; null elsewhere).
+// contexts; null elsewhere).  seq is stored last, after a system-scope
+// fence, so a host that sees the step's seq also sees its u0 and status.
 struct HostOut {
   double u0[2];  // u*_0
   int status;    // kStatus*
-  int pad;
+  int seq;       // low 32 bits of the step's iteration counter + 1
 };
 
 // Everything a CTA needs to process one tile of one controller.

@@ -533,6 +533,8 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
         D.host_out->u0[0] = us0[0];
         D.host_out->u0[1] = us0[1];
         D.host_out->status = *reinterpret_cast<volatile int*>(&st->status);
+        __threadfence_system();
+        *reinterpret_cast<volatile int*>(&D.host_out->seq) = (int)(uint32_t)(ts.iter + 1ull);
       }
       constexpr int n = Dyn<MODEL>::n;
       double xn[6] = {0, 0, 0, 0, 0, 0};
