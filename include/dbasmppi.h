@@ -177,19 +177,22 @@ int mppi_set_grid(mppi_ctx* c, const float* sdf, int32_t nx, int32_t ny, double 
 int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream);
 
 /* One iteration from device data (x0, xref in device memory, same layout;
- * xref must not be NULL).  Enqueues only the step kernel. */
+ * xref must not be NULL).  Enqueues only the step kernel, which writes no
+ * host mirror: a following mppi_get_control copies u0 from device memory
+ * and synchronises. */
 int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref,
                      void* stream);
 
 /* After a step: u0 = u*_0 (2 doubles, the control to apply) and, if U is
  * not NULL, the shifted nominal sequence for the next step (T x 2).
- * u0 and the status word are written by the step itself into mapped pinned
- * host memory, followed (after a system-scope fence) by the step's
- * iteration number.  With U NULL the call returns as soon as that number
- * shows the last enqueued step, which can be before its kernel has retired;
- * the stream keeps the order of later work.  If the stream ends without it
- * (an error), or when U is asked for, it synchronises with the context's
- * last stream (U is then copied).  Errors: MPPI_ESTATE (no step has run),
+ * After mppi_step, u0 and the status word are written by the step itself
+ * into mapped pinned host memory, followed (after a system-scope fence) by
+ * the step's iteration number.  With U NULL the call then returns as soon
+ * as that number shows the last enqueued step, which can be before its
+ * kernel has retired; the stream keeps the order of later work.  If the
+ * stream ends without it (an error), when U is asked for, or after
+ * mppi_step_device, it synchronises with the context's last stream and
+ * copies what the mirror does not hold.  Errors: MPPI_ESTATE (no step has run),
  * MPPI_ETIMEOUT (a bounded device wait of the step expired), MPPI_ECUDA. */
 int mppi_get_control(mppi_ctx* c, double* u0, double* U);
 

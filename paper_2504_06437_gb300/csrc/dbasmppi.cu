@@ -341,6 +341,7 @@ struct mppi_ctx {
   cudaStream_t own = nullptr;
   cudaStream_t last = nullptr;
   bool stepped = false;
+  bool mirrored = false;  // the last step writes the host mirror (mppi_step)
   uint64_t iter = 0;  // iteration counter of the device state after the steps enqueued so far
 };
 
@@ -745,16 +746,34 @@ int mppi_set_grid(mppi_ctx* c, const float* sdf, int32_t nx, int32_t ny, double 
   return MPPI_OK;
 }
 
-int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref, void* stream) {
-  if (!c) return fail(MPPI_ESTATE, "context is NULL");
-  if (!d_x0 || !d_xref) return fail(MPPI_EINVAL, "device x0 / xref must not be NULL");
+namespace {
+// Enqueue one step.  mirror: the final stage writes u0, the status and the
+// fenced sequence word to the mapped host mirror (mppi_step, whose caller
+// reads the control on the host); the device-input entry point leaves it
+// out, since the system-scope fence adds the host link's round trip to the
+// kernel's retirement.
+int launch_step(mppi_ctx* c, const double* x0, const double* xref, void* stream, bool mirror) {
   cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
-  c->fn<<<c->D.nTiles, c->tl.threads, c->smem, s>>>(c->D, d_x0, d_xref);
+  if (mirror) {
+    c->fn<<<c->D.nTiles, c->tl.threads, c->smem, s>>>(c->D, x0, xref);
+  } else {
+    CtrlDesc D = c->D;
+    D.host_out = nullptr;
+    c->fn<<<c->D.nTiles, c->tl.threads, c->smem, s>>>(D, x0, xref);
+  }
   CK(cudaGetLastError());
   c->last = s;
   c->stepped = true;
+  c->mirrored = mirror;
   ++c->iter;
   return MPPI_OK;
+}
+}  // namespace
+
+int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref, void* stream) {
+  if (!c) return fail(MPPI_ESTATE, "context is NULL");
+  if (!d_x0 || !d_xref) return fail(MPPI_EINVAL, "device x0 / xref must not be NULL");
+  return launch_step(c, d_x0, d_xref, stream, false);
 }
 
 int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream) {
@@ -773,7 +792,7 @@ int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream) {
   } else {
     for (int t = 0; t <= T; ++t) memcpy(h + n + t * n, c->p.x_goal, sizeof(double) * n);
   }
-  const int rc = mppi_step_device(c, c->h_in_dev[b], c->h_in_dev[b] + n, s);
+  const int rc = launch_step(c, c->h_in_dev[b], c->h_in_dev[b] + n, s, true);
   if (rc) return rc;
   CK(cudaEventRecord(c->in_ev[b], s));
   c->in_ev_pending[b] = true;
@@ -786,7 +805,7 @@ int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
   if (!c->stepped) return fail(MPPI_ESTATE, "no step has run");
   // u0 and the status word come from the mapped mirror the step's final
   // stage wrote; only U, when asked for, is copied
-  if (!U) {
+  if (!U && c->mirrored) {
     // the last step's final stage stores seq after its u0 and status (and a
     // system-scope fence): once seq shows that step, the mirror holds its
     // output, without waiting for the kernel to retire.  The stream is
@@ -810,12 +829,17 @@ int mppi_get_control(mppi_ctx* c, double* u0, double* U) {
     }
   }
   if (U) CK(cudaMemcpyAsync(c->h_U, c->d_U, sizeof(double) * 2 * c->p.T, cudaMemcpyDeviceToHost, c->last));
+  // a step with device inputs wrote no mirror: u0 and the status come from
+  // the device state
+  if (!c->mirrored)
+    CK(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, c->last));
   CK(cudaStreamSynchronize(c->last));
-  if (c->h_out->status == kStatusTimeout)
+  const int status = c->mirrored ? c->h_out->status : c->h_st->status;
+  if (status == kStatusTimeout)
     return fail(MPPI_ETIMEOUT, "a bounded device wait (obstacle staging) expired");
   if (u0) {
-    u0[0] = c->h_out->u0[0];
-    u0[1] = c->h_out->u0[1];
+    u0[0] = c->mirrored ? c->h_out->u0[0] : c->h_st->u0[0];
+    u0[1] = c->mirrored ? c->h_out->u0[1] : c->h_st->u0[1];
   }
   if (U) memcpy(U, c->h_U, sizeof(double) * 2 * c->p.T);
   return MPPI_OK;
