@@ -505,3 +505,38 @@ def test_grid_other_models(gpu, orc, name):
     g = W.sdf_grid(w.obstacles, [], lo[0], lo[1], res, nx, ny)
     p = dict(w.params, grid=g, grid_ox=float(lo[0]), grid_oy=float(lo[1]), grid_res=res)
     run_pair(gpu, orc, dataclasses.replace(w, params=p, obstacles=np.zeros((0, 3))), steps=2)
+
+
+def test_control_readback_paths(gpu):
+    """mppi_get_control after host-input steps (it returns once the step's
+    fenced sequence word reaches the host mirror) and after device-input
+    steps (no mirror: u0 copied from device memory) returns exactly the
+    step's u*_0, a fresh one every step; after mppi_set_state to an earlier
+    state, the same inputs give the same control again."""
+    torch = pytest.importorskip("torch")
+    w = W.quad2d(4, K=1024, T=30)
+    xs = [w.x_start + 0.03 * i for i in range(6)]
+    refs = [w.reference(x) for x in xs]
+    with gpu.Controller(w.params) as g:
+        g.set_obstacles(w.obstacles)
+        seen, saved = [], None
+        for i, (x, xr) in enumerate(zip(xs, refs)):
+            if i == 3:
+                saved = g.get_state()
+            if i % 2 == 0:
+                g.step(x, xr)
+            else:
+                d = torch.tensor(np.concatenate([x, xr.ravel()]), dtype=torch.float64,
+                                 device="cuda")
+                g.step_device(d.data_ptr(), d.data_ptr() + 8 * len(x))
+            u0 = g.get_control()
+            dbg = g.get_debug()
+            np.testing.assert_array_equal(u0, dbg["Ustar"][0])
+            assert dbg["iter"] == i + 1
+            seen.append(u0.copy())
+        assert len({tuple(u) for u in seen}) == len(seen)
+        g.set_state(saved["U"], saved["S_e"], saved["beta"], saved["first"], saved["iter"])
+        g.step(xs[3], refs[3])
+        np.testing.assert_array_equal(g.get_control(), seen[3])
+        g.step(xs[4], refs[4])
+        np.testing.assert_array_equal(g.get_control(), seen[4])
