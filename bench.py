@@ -236,8 +236,56 @@ def describe(world):
                if p.get("grid") is not None else {})}
 
 
+def run_reference_mix(args):
+    """The oracle on the batched or served mix: one reference step is one
+    oracle step of each of the first controllers of the mix, each on a
+    bounded sample of its K samples (the mix is far too large for a CPU
+    step of every controller)."""
+    from paper_2504_06437_gb300 import workloads as W
+    import oracle
+    serving = args.workload == "serving"
+    worlds = (W.serving_mix(args.robots, seed=0) if serving else W.batch_mix(args.batch_n, seed=0))
+    worlds = worlds[:8]
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    jobs = []
+    for w in worlds:
+        pp = dict(w.params)
+        pp["K"] = min(int(pp["K"]), args.ref_samples)
+        jobs.append((w, pp, oracle.new_controller(pp), w.reference(w.x_start)))
+    def one():
+        for w, pp, ctl, xr in jobs:
+            oracle.step(pp, w.obstacles, w.x_start, xr, ctl)
+    for _ in range(max(args.warmup, 3)):
+        one()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    work = sum(int(pp["K"]) * int(pp["T"]) for _, pp, _, _ in jobs)
+    value = work / (ms / 1e3)
+    sample = (f"oracle step of the first {len(jobs)} controllers of the mix, "
+              f"{args.ref_samples} samples each at most, {args.steps} steps")
+    line = {"impl": "reference",
+            "metric": METRIC + (" and p50/p99 step latency (serving)" if serving else " (batched)"),
+            "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": ("serving_mix" if serving else "batch_mix")
+                       + f": the first {len(jobs)} controllers"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
+        return
+    if args.workload in ("batch_mix", "serving"):
+        run_reference_mix(args)
         return
     world = world_for(args.workload, 0, args.sgf)
     p = world.params
