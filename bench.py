@@ -1,8 +1,11 @@
 """Benchmark of one DBaS-Log-MPPI step (arXiv 2504.06437) on GB300.
 
 Metric: sample-timesteps per second of one MPPI iteration (K samples x T
-steps / step time) on the planar-quadrotor workload (K=4096, T=50,
-40 obstacles, 7 shape points), with p50/p99 step latency.
+steps / step time), with p50/p99 step latency, batched vs plain.  The
+default line is the large single-controller workload (kinematic unicycle,
+K=65536, T=100, 200 obstacles in a 50 x 50 m field), and it carries, under
+"batched", the batched-vs-plain comparison on the 512-controller mix (one
+persistent launch against one launch per controller).
 
 * value: device-resident inputs, one step = one kernel launch
   (mppi_step_device); each step timed with CUDA events on the launching
@@ -36,7 +39,11 @@ if ROOT not in sys.path:
 
 METRIC = "sample-timesteps/sec per MPPI step"
 UNIT = "sample-steps/s"
-OPS_PER_PAIR = 8          # 2 sub, 2 fma (h), max (floor), rcp, add, min (collision)
+# FP32-pipe operations per obstacle-point pair: 2 subtractions and 2 fmas for
+# h, the reciprocal, the add into the sum and the min of the collision test
+# (7); the h_eps floor's max, an eighth, is reported beside it
+OPS_PER_PAIR = 7
+OPS_PER_PAIR_WITH_FLOOR = 8
 OPS_PER_SAMPLE_STEP = 135  # Philox (~80), NLN map (~20), dynamics + costs (~35)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -47,9 +54,16 @@ L2_FLUSH_BYTES = 256 << 20
 OPS_PER_GRID_POINT = 24
 
 
-def algorithmic_ops(K, T, P, J, grid=False):
-    return K * T * (OPS_PER_PAIR * P * J + (OPS_PER_GRID_POINT * P if grid else 0)
+def algorithmic_ops(K, T, P, J, grid=False, per_pair=OPS_PER_PAIR):
+    return K * T * (per_pair * P * J + (OPS_PER_GRID_POINT * P if grid else 0)
                     + OPS_PER_SAMPLE_STEP)
+
+
+def io_bytes_per_launch(K, T, n, J):
+    """Bytes one step must move at least: x0, the reference, U and the
+    obstacles in; the shifted U, U*, the per-sample costs (FP64) and
+    collided flags out."""
+    return 8 * (n + (T + 1) * n) + 8 * 2 * T + 24 * J + 2 * 8 * 2 * T + 9 * K
 
 
 def kernel_src_sha():
@@ -324,10 +338,12 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, ws, rank, local):
+def measure_batch(args, ws, rank, local):
     """Batched workload: many controllers of mixed model, K, T and obstacle
     count stepped by one persistent launch (CUDA graph replay), against the
-    same controllers stepped one launch each, back to back on one stream."""
+    same controllers stepped one launch each, back to back on one stream,
+    and against the host loop that steps each and reads its control back.
+    Returns the measurements (every rank), or None on ranks other than 0."""
     import torch
     from paper_2504_06437_gb300 import binding, workloads as W
 
@@ -353,13 +369,14 @@ def run_batch(args, ws, rank, local):
     for _ in range(args.warmup):
         b.step(slots, x0s, xrefs, stream)
         b.controls()
+    steps = args.batch_steps
     sampler = ClockSampler()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     wall = []
     barrier(ws)
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(float(i & 7))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -389,7 +406,8 @@ def run_batch(args, ws, rank, local):
         g.step_device(d_in.data_ptr(), d_in.data_ptr() + 8 * n, stream)
     torch.cuda.synchronize()
     p_ms = []
-    for i in range(max(3, args.steps // 10)):
+    psampler = ClockSampler()
+    for i in range(max(3, steps // 10)):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         c = torch.cuda.Event(enable_timing=True)
@@ -399,7 +417,8 @@ def run_batch(args, ws, rank, local):
         c.record(stream)
         torch.cuda.synchronize()
         p_ms.append(a.elapsed_time(c))
-    plain_ms = float(np.mean(p_ms))
+    pclocks = psampler.stop()
+    plain_ms = allmax(ws, float(np.mean(p_ms)))
     # and the naive host loop: each controller stepped from host data and its
     # control read back before the next (mppi_step + mppi_get_control)
     xr_host = [w.reference(w.x_start) for w in worlds]
@@ -409,41 +428,47 @@ def run_batch(args, ws, rank, local):
     for (g, _, _), w, xr in zip(plain, worlds, xr_host):
         g.step(w.x_start, xr, stream)
         g.get_control()
-    synced_ms = 1e3 * (time.perf_counter() - t0)
+    synced_ms = allmax(ws, 1e3 * (time.perf_counter() - t0))
     for g, _, _ in plain:
         g.close()
     b.close()
     if rank != 0:
-        return
+        return None
     # the same FP32 issue roofline as the one-controller step, over the sum
     # of the controllers' algorithmic work (the batch kernel is the only
     # kernel in the timed region)
-    ops = sum(algorithmic_ops(int(w.params["K"]), int(w.params["T"]),
-                              int(np.asarray(w.params["shape"]).reshape(-1, 2).shape[0]),
-                              int(w.obstacles.shape[0])) for w in worlds)
+    def ops(per_pair):
+        return sum(algorithmic_ops(int(w.params["K"]), int(w.params["T"]),
+                                   int(np.asarray(w.params["shape"]).reshape(-1, 2).shape[0]),
+                                   int(w.obstacles.shape[0]), per_pair=per_pair) for w in worlds)
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tops = sms * 128 * f_max / 1e12
-    achieved_tops = ops / (ms / 1e3) / 1e12
+    achieved_tops = ops(OPS_PER_PAIR) / (ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TOP/s",
-                "frac": achieved_tops / peak_tops, "traffic": None, "kernel": "batch_kernel",
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz",
-                "ops_per_launch": ops}
-    line = {"metric": METRIC + " (batched)", "value": whole_job_value(ws, work, ms), "unit": UNIT,
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"batch_mix: {len(worlds)} controllers, half unicycle half planar "
-                                   "quadrotor, K log-uniform 1024..16384, T 20..80, 5..300 obstacles",
-                       "sample_steps_per_step": work, "l2": "flushed between timed steps (256 MB write)",
-                       "graph": "CUDA graph replay of copy-in, persistent kernel, copy-out",
-                       "tiling_policy": used_policy,
-                       "tiling_source": "autotuned (mppi_batch_autotune)" if policy else "default"},
-            "latency_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
-            "plain": {"value": work / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
-                      "form": "one launch per controller, back to back on one stream"},
-            "plain_synced": {"value": work / (synced_ms / 1e3), "unit": UNIT, "ms_per_step": synced_ms,
+                "frac": achieved_tops / peak_tops, "traffic": traffic_per_launch("batch_mix"),
+                "kernel": "batch_kernel",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz (of measured max clock)",
+                "ops_per_launch": ops(OPS_PER_PAIR),
+                "ops_count": f"{OPS_PER_PAIR} per obstacle-point pair + {OPS_PER_SAMPLE_STEP} per sample-step",
+                "frac_with_floor_op": ops(OPS_PER_PAIR_WITH_FLOOR) / (ms / 1e3) / 1e12 / peak_tops}
+    return {"value": whole_job_value(ws, work, ms), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "warmup": args.warmup,
+            "workload": f"batch_mix: {len(worlds)} controllers, half unicycle half planar "
+                        "quadrotor, K log-uniform 1024..16384, T 20..80, 5..300 obstacles",
+            "sample_steps_per_step": work, "l2": "flushed between timed steps (256 MB write)",
+            "graph": "CUDA graph replay of copy-in, persistent kernel, copy-out",
+            "tiling_policy": used_policy,
+            "tiling_source": "autotuned (mppi_batch_autotune)" if policy else "default",
+            "latency_ms": {"p50": float(np.percentile(dev_ms, 50)),
+                           "p99": float(np.percentile(dev_ms, 99))},
+            "plain": {"value": whole_job_value(ws, work, plain_ms), "unit": UNIT,
+                      "ms_per_step": plain_ms, "steps": len(p_ms),
+                      "form": "one launch per controller, back to back on one stream",
+                      "clocks": pclocks},
+            "plain_synced": {"value": whole_job_value(ws, work, synced_ms), "unit": UNIT,
+                             "ms_per_step": synced_ms,
                              "form": "host loop: mppi_step + mppi_get_control per controller"},
             "batched_over_plain": plain_ms / ms,
             "batched_over_plain_synced": synced_ms / ms,
@@ -452,8 +477,23 @@ def run_batch(args, ws, rank, local):
                     "d2h_bytes_per_step": 16 * len(worlds),
                     "latency_ms": {"p50": 1e3 * float(np.percentile(wall, 50)),
                                    "p99": 1e3 * float(np.percentile(wall, 99))}},
-            "roofline": roofline,
-            "gpu_launches": args.steps, "clocks": clocks}
+            "roofline": roofline, "gpu_launches": steps, "clocks": clocks}
+
+
+def run_batch(args, ws, rank, local):
+    """The batched workload as its own line (--workload batch_mix)."""
+    m = measure_batch(args, ws, rank, local)
+    if m is None:
+        return
+    line = {"metric": METRIC + " (batched)", "value": m["value"], "unit": UNIT,
+            "n_gpus": ws, "steps": m["steps"], "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {k: m[k] for k in ("workload", "sample_steps_per_step", "l2", "graph",
+                                         "tiling_policy", "tiling_source")},
+            **{k: m[k] for k in ("latency_ms", "plain", "plain_synced", "batched_over_plain",
+                                 "batched_over_plain_synced", "e2e", "roofline", "gpu_launches",
+                                 "clocks")}}
     print(json.dumps(line), flush=True)
 
 
@@ -521,7 +561,9 @@ def run_serving(args, ws, rank, local):
     st1 = srv.stats()
     cap_rps = cap["requests"] / cap["seconds"]
     think = len(worlds) / (args.load * cap_rps)
+    sampler = ClockSampler()
     loaded = run(args.serve_steps, think)
+    clocks = sampler.stop()
     st2 = srv.stats()
     srv.close()
     # plain: the same kind of requests served one at a time
@@ -564,7 +606,8 @@ def run_serving(args, ws, rank, local):
                       "form": "one request at a time: mppi_step + mppi_get_control",
                       "requests": len(plain_lat),
                       "latency_ms": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99)}},
-            "serving_over_plain": (cap["work"] / cap["seconds"]) / (plain_work / plain_s)}
+            "serving_over_plain": (cap["work"] / cap["seconds"]) / (plain_work / plain_s),
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -574,7 +617,11 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="quad2d")
+    ap.add_argument("--workload", default="unicycle_stress")
+    ap.add_argument("--batch-steps", type=int, default=20,
+                    help="timed steps of the batched comparison")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched-vs-plain comparison out of the default line")
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-samples", type=int, default=256)
@@ -596,6 +643,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch_mix":
+        args.batch_steps = args.steps
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -686,17 +735,27 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tops = sms * 128 * f_max / 1e12
-    achieved_tops = algorithmic_ops(K, T, P, J, has_grid) / (ms_local / 1e3) / 1e12
+    ops_launch = algorithmic_ops(K, T, P, J, has_grid)
+    achieved_tops = ops_launch / (ms_local / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TOP/s",
                 "frac": achieved_tops / peak_tops, "traffic": traffic_per_launch(world.name),
-                "kernel": "step_kernel", "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz",
-                "ops_per_launch": algorithmic_ops(K, T, P, J, has_grid)}
+                "kernel": "step_kernel",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {f_max/1e6:.0f} MHz (of measured max clock)",
+                "ops_per_launch": ops_launch,
+                "ops_count": f"{OPS_PER_PAIR} per obstacle-point pair + {OPS_PER_SAMPLE_STEP} per sample-step",
+                "frac_with_floor_op": algorithmic_ops(K, T, P, J, has_grid, OPS_PER_PAIR_WITH_FLOOR)
+                / (ms_local / 1e3) / 1e12 / peak_tops,
+                "algorithmic_bytes_per_launch": io_bytes_per_launch(K, T, n, J)}
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved_tops / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
-    load_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
-    if load_mhz:  # the pool's median SM clock under a power-capped GEMM load
-        roofline["frac_at_measured_load_clock"] = achieved_tops / (sms * 128 * load_mhz * 1e6 / 1e12)
-        roofline["measured_load_clock_mhz"] = load_mhz
+    batched = None
+    if args.workload == "unicycle_stress" and not args.no_batch:
+        # the other half of the metric, batched vs plain, in the same line
+        # (every rank takes part: the measurement has barriers)
+        ctl.close()
+        del d_in, flush
+        torch.cuda.empty_cache()
+        batched = measure_batch(args, ws, rank, local)
 
     if rank != 0:
         return
@@ -712,6 +771,8 @@ def main():
                     "latency_ms": {"p50": 1e3 * float(np.percentile(e2e_t, 50)),
                                    "p99": 1e3 * float(np.percentile(e2e_t, 99))}},
             "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline}
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu_baseline and ws == 1:
         threads = os.cpu_count() or 1
         rate, steps, el, used = oracle_rate(world, min(K, args.ref_samples), args.cpu_seconds,

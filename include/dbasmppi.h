@@ -137,8 +137,12 @@ int mppi_create(const mppi_params* p, const double* u_init, mppi_ctx** out);
 int mppi_create_tiled(const mppi_params* p, const double* u_init,
                       const mppi_tiling* tiling, mppi_ctx** out);
 
-/* Replace the obstacle set.  cxcyr: J x 3 (centre x, centre y, radius) in
- * the world frame; copied.  J may be 0 (empty set, barrier sum 0).  Errors:
+/* Replace the obstacle set: the circles {c_j, r_j} of the constraint
+ * functions h_j(x) = |p - c_j|^2 - r_j^2 of Eq. 13 (quadrotor) and Eq. 15
+ * (vehicle), evaluated at every shape point p of the body, whose barrier
+ * terms B(h) = 1/h enter the barrier state of Eq. 7.  cxcyr: J x 3 (centre
+ * x, centre y, radius) in the world frame; copied.  J may be 0 (empty set,
+ * barrier sum 0).  Errors:
  * MPPI_EINVAL (J < 0, J > MPPI_MAX_OBSTACLES, non-finite value, radius < 0,
  * |cx|, |cy| or r above MPPI_MAX_COORD).
  * Synchronises with the context's last stream before replacing the set. */
@@ -183,8 +187,10 @@ int mppi_step(mppi_ctx* c, const double* x0, const double* xref, void* stream);
 int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref,
                      void* stream);
 
-/* After a step: u0 = u*_0 (2 doubles, the control to apply) and, if U is
- * not NULL, the shifted nominal sequence for the next step (T x 2).
+/* After a step: u0 = u*_0 (2 doubles), the control Algorithm 1 actuates on
+ * the plant after the update (first element of U* of Eq. 4), and, if U is
+ * not NULL, the shifted nominal sequence for the next step (T x 2; the
+ * shift of Algorithm 1's last loop, the last element repeated).
  * After mppi_step, u0 and the status word are written by the step itself
  * into mapped pinned host memory, followed (after a system-scope fence) by
  * the step's iteration number.  With U NULL the call then returns as soon
@@ -285,10 +291,15 @@ int mppi_debug_wait_probe(int64_t max_cycles, int32_t arrive);
  *   d_u0     device out, 2 doubles: u*_0.
  *   d_costs  device out, K doubles, or NULL.
  * All work is enqueued on `stream` (NULL = the legacy default stream); the
- * call returns without waiting.  The first call on each device looks up the
- * array's device address and sets kernel attributes, so make it before any
- * stream capture.  Every call shares the one array: calls whose GPU work
- * overlaps (other streams, other host threads) race; order them.  Errors:
+ * call returns without waiting.  Set-up happens on first use, not at load:
+ * the first call on each device looks up the array's device address (once,
+ * under a lock, so host threads may race to it), and the first call for each
+ * (device, model, smoothing on or off) sets that step kernel's shared-memory
+ * limit and queries its occupancy; a new launch shape queries occupancy
+ * again.  Make one such call for every (device, model, smoothing) you will
+ * use before any stream capture.  Every call shares the one array: calls
+ * whose GPU work overlaps (other streams, other host threads) race; order
+ * them.  Errors:
  * MPPI_EINVAL (bad params, NULL pointer, or a problem whose scratch exceeds
  * the 8 MiB limit -- the message gives the bytes needed), MPPI_ECUDA. */
 int mppi_step_static(const mppi_params* p, const double* d_obst, int32_t J,

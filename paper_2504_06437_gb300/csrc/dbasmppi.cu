@@ -1002,6 +1002,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 constexpr int kMaxStaticDevices = 64;
 unsigned char* g_static_base[kMaxStaticDevices] = {nullptr};  // device address, per device
+std::mutex g_static_mu;  // guards the set-up of g_static_base
 
 // Device-side copy of the caller's controller state into the scratch state
 // block, ticket counters and minimum words cleared, constants derived; the caller's ctl is
@@ -1055,13 +1056,18 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxStaticDevices) return fail(MPPI_EINVAL, "device %d out of range", dev);
-  if (!g_static_base[dev]) {
-    // set-up, once per device, with that device current
-    void* base = nullptr;
-    CK(cudaGetSymbolAddress(&base, g_static_scratch));
-    g_static_base[dev] = (unsigned char*)base;
+  unsigned char* base = nullptr;
+  {
+    // set-up, once per device, with that device current; the lock makes the
+    // first calls of several host threads safe
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[dev]) {
+      void* a = nullptr;
+      CK(cudaGetSymbolAddress(&a, g_static_scratch));
+      g_static_base[dev] = (unsigned char*)a;
+    }
+    base = g_static_base[dev];
   }
-  unsigned char* base = g_static_base[dev];
   mppi_ctx c;  // on the stack: only its descriptor logic is used
   c.p = *p;
   c.n = state_dim(p->model);
@@ -1694,19 +1700,38 @@ int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, cons
   } else {
     drop_lane_graph(L);
     if (allow_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaMemcpyAsync(L.d_stage, L.h_stage, bytes, cudaMemcpyHostToDevice, st);
-    kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, L.d_stage, L.d_out);
-    cudaMemcpyAsync(L.h_out, L.d_out, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st);
+    // every call checked; once a capture has begun it is ended on every path
+    cudaError_t e = cudaMemcpyAsync(L.d_stage, L.h_stage, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      kernel<<<grid, kBatchThreads, smem, st>>>(b->d_descs, L.d_stage, L.d_out);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(L.h_out, L.d_out, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st);
     if (allow_graph) {
-      CK(cudaStreamEndCapture(st, &L.graph));
-      CK(cudaGraphInstantiate(&L.gexec, L.graph, 0));
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(st, &g);
+      if (e == cudaSuccess) e = ec;
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(MPPI_ECUDA, "batched step capture failed: %s", cudaGetErrorString(e));
+      }
+      L.graph = g;
+      e = cudaGraphInstantiate(&L.gexec, L.graph, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        drop_lane_graph(L);
+        return fail(MPPI_ECUDA, "batched step graph instantiation failed: %s",
+                    cudaGetErrorString(e));
+      }
       L.graph_key = key;
       L.graph_bytes = bytes;
       L.graph_smem = smem;
       L.graph_grid = grid;
       CK(cudaGraphLaunch(L.gexec, st));
-    } else {
-      CK(cudaGetLastError());
+    } else if (e != cudaSuccess) {
+      return fail(MPPI_ECUDA, "batched step launch failed: %s", cudaGetErrorString(e));
     }
   }
   L.last = st;
@@ -1947,12 +1972,17 @@ struct mppi_server {
   std::atomic<bool> stop{false};
   std::atomic<unsigned long long> batches{0}, requests{0};
   std::atomic<int> n_inflight{0};
+  int device = 0;  // the device current at mppi_server_create, where the pool lives
   char err[512] = "";
 };
 
 namespace {
 
 void server_loop(mppi_server* sv) {
+  // a new host thread starts on device 0: take the server's device, where
+  // its pool, streams and events were made, before any other CUDA call
+  const bool dev_ok = cudaSetDevice(sv->device) == cudaSuccess;
+  if (!dev_ok) cudaGetLastError();  // every request then completes with MPPI_ECUDA
   std::vector<int32_t> slots;
   std::vector<double> x0s;
   std::vector<const double*> xr;
@@ -2000,8 +2030,10 @@ void server_loop(mppi_server* sv) {
         memcpy(&x0s[(size_t)j * 6], batch[j].x0, sizeof(double) * 6);
         xr[j] = batch[j].xref.empty() ? nullptr : batch[j].xref.data();
       }
-      int rc = lane_step(sv->b, sv->lanes[i], slots.data(), n, x0s.data(), xr.data(),
-                         sv->streams[i], false);
+      int rc = dev_ok ? lane_step(sv->b, sv->lanes[i], slots.data(), n, x0s.data(), xr.data(),
+                                  sv->streams[i], false)
+                      : fail(MPPI_ECUDA, "cudaSetDevice(%d) failed in the scheduler thread",
+                             sv->device);
       if (rc == MPPI_OK) rc = cudaEventRecord(sv->events[i], sv->streams[i]) == cudaSuccess
                                   ? MPPI_OK : MPPI_ECUDA;
       if (rc != MPPI_OK) {
@@ -2038,6 +2070,10 @@ int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes, mpp
   if (lanes < 1 || lanes > 8) return fail(MPPI_EINVAL, "lanes must be in [1, 8]");
   mppi_server* sv = new (std::nothrow) mppi_server();
   if (!sv) return fail(MPPI_ENOMEM, "host allocation failed");
+  if (cudaGetDevice(&sv->device) != cudaSuccess) {
+    delete sv;
+    return fail(MPPI_ECUDA, "cudaGetDevice failed");
+  }
   int rc = mppi_batch_create(max_robots, pool_bytes, &sv->b);
   if (rc) {
     delete sv;

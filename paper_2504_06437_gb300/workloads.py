@@ -16,6 +16,8 @@ so these fields stand in for its missions:
   0.981 N).
 * ``unicycle_stress``: 50 x 50 m field, 200 obstacles, r ~ U(0.1, 1.0) m,
   K=65536, T=100.
+* ``quad2d_corridor``: ``quad2d`` with six of its circles moved onto the
+  flight line just ahead of the start, so that many samples collide.
 * ``batch_mix`` / ``serving_mix``: many independent controllers with mixed
   model, K, T and obstacle count.
 
@@ -84,6 +86,35 @@ def obstacle_field(g: np.random.Generator, J: int, lo, hi, r_lo: float,
             c = lo + (hi - lo) * g.random(2)
             r = r_lo + (r_hi - r_lo) * g.random()
             if all(np.hypot(*(c - np.asarray(p[:2]))) > r + clearance for p in keep_clear):
+                break
+        out[j] = (c[0], c[1], r)
+    return out
+
+
+def corridor_obstacles(g: np.random.Generator, J: int, start, goal, shape,
+                       along, lateral, r_lo: float, r_hi: float,
+                       margin: float = 0.05) -> np.ndarray:
+    """J circles (cx, cy, r) placed across the start-goal line: centres at a
+    distance uniform in ``along`` from the start along the line and offset
+    uniformly within +-``lateral`` across it, radii uniform in [r_lo, r_hi];
+    a circle closer than r + margin to a shape point of the body at the
+    start pose, or than r + 0.5 to the goal, is redrawn.  These put
+    obstacles where the sampled trajectories go, so that many samples
+    collide."""
+    a = np.asarray(start[:2], dtype=np.float64)
+    d = np.asarray(goal[:2], dtype=np.float64) - a
+    d /= np.hypot(*d)
+    nrm = np.array([-d[1], d[0]])
+    th = float(start[2]) if len(start) > 2 else 0.0
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    body = a + np.asarray(shape, dtype=np.float64).reshape(-1, 2) @ R.T
+    out = np.zeros((J, 3))
+    for j in range(J):
+        for _ in range(10000):
+            c = a + g.uniform(*along) * d + g.uniform(-lateral, lateral) * nrm
+            r = g.uniform(r_lo, r_hi)
+            if (np.hypot(*(body - c).T).min() > r + margin
+                    and np.hypot(*(c - np.asarray(goal[:2]))) > r + 0.5):
                 break
         out[j] = (c[0], c[1], r)
     return out
@@ -210,6 +241,21 @@ def unicycle_stress(seed: int = 0, K: int = 65536, T: int = 100) -> World:
     return World(p, obs, start, goal, v_ref=2.0, name="unicycle_stress")
 
 
+def quad2d_corridor(seed: int = 0, K: int = 4096, T: int = 50, n_corridor: int = 6) -> World:
+    """The ``quad2d`` world with its first ``n_corridor`` circles moved onto
+    the flight line 0.7 to 2 m ahead of the hovering start (offsets within
+    +-1 m across it, r ~ U(0.2, 0.6) m, clear of the body at the start): the
+    sampled trajectories reach them within the horizon, and about 40 % of
+    the samples of the first step collide.  Same sizes as ``quad2d``
+    (J = 40, P = 7)."""
+    w = quad2d(seed, K=K, T=T)
+    g = rng(seed + 1001)
+    obs = w.obstacles.copy()
+    obs[:n_corridor] = corridor_obstacles(g, n_corridor, w.x_start, w.goal, w.params["shape"],
+                                          (0.7, 2.0), 1.0, 0.2, 0.6)
+    return World(w.params, obs, w.x_start, w.goal, w.v_ref, name="quad2d_corridor")
+
+
 def _mixed_world(g: np.random.Generator, idx: int, seed: int, K_lo: int,
                  K_hi: int, T_lo: int, T_hi: int, J_lo: int, J_hi: int) -> World:
     model = UNICYCLE if idx % 2 == 0 else QUAD2D
@@ -323,6 +369,7 @@ def ackermann_grid(seed: int = 0, K: int = 1024, T: int = 20, res: float = 0.1) 
 PRESETS = {
     "unicycle_small": unicycle_small,
     "quad2d": quad2d,
+    "quad2d_corridor": quad2d_corridor,
     "unicycle_stress": unicycle_stress,
     "ackermann": ackermann,
     "quad5": quad5,

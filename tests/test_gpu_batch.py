@@ -108,25 +108,25 @@ def test_admission_by_memory(gpu):
 
 
 def test_batch_matches_oracle(gpu, orc):
-    worlds = [W.unicycle_small(1), W.quad2d(1, K=700, T=30)]
-    with gpu.Batch(4, 128 << 20) as b:
+    """One batched step of all four models and a smoothed controller (window
+    9, order 3) against the oracle, from the same inputs: per-sample costs,
+    u*_0 and the shifted sequence of every slot."""
+    worlds = [W.unicycle_small(1), W.quad2d(1, K=700, T=30), W.ackermann(1), W.quad5(1),
+              W.quad2d(2, K=500, T=24)]
+    worlds[-1].params.update(sgf_window=9, sgf_order=3)
+    with gpu.Batch(len(worlds), 256 << 20) as b:
         slots = [b.add(w.params, w.obstacles) for w in worlds]
-        for step in range(2):
-            ctls = [orc.new_controller(w.params) for w in worlds] if step == 0 else ctls
-            if step > 0:
-                # identical inputs for the second step: resynchronise is not
-                # possible in the batch API, so only the first step is compared
-                break
-            xrefs = [w.reference(w.x_start) for w in worlds]
-            b.step(slots, [w.x_start for w in worlds], xrefs)
-            u = b.controls()
-            for i, (w, s) in enumerate(zip(worlds, slots)):
-                ro = orc.step(w.params, w.obstacles, w.x_start, xrefs[i], ctls[i])
-                st = b.state(s)
-                rel = np.abs(st["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
-                assert rel.max() <= 1e-4
-                np.testing.assert_allclose(u[i], ro["u0"], rtol=0, atol=1e-5)
-                np.testing.assert_allclose(st["U"], ro["U_next"], rtol=0, atol=1e-5)
+        ctls = [orc.new_controller(w.params) for w in worlds]
+        xrefs = [w.reference(w.x_start) for w in worlds]
+        b.step(slots, [w.x_start for w in worlds], xrefs)
+        u = b.controls()
+        for i, (w, s) in enumerate(zip(worlds, slots)):
+            ro = orc.step(w.params, w.obstacles, w.x_start, xrefs[i], ctls[i])
+            st = b.state(s)
+            rel = np.abs(st["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
+            assert rel.max() <= 1e-4, (i, rel.max())
+            np.testing.assert_allclose(u[i], ro["u0"], rtol=0, atol=1e-5, err_msg=str(i))
+            np.testing.assert_allclose(st["U"], ro["U_next"], rtol=0, atol=1e-5, err_msg=str(i))
 
 
 def test_batch_autotuned_policy_shapes_and_equals_alone(gpu):

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2504_06437_gb300 import workloads as W
+from weight_checks import check_weights
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +33,7 @@ def gpu():
     return binding
 
 
-def compare_step(ro, dbg, u0, U_next, label=""):
+def compare_step(ro, dbg, u0, U_next, label="", lam=1.0):
     S_o, S_g = ro["costs"], dbg["costs"]
     rel = np.abs(S_g - S_o) / np.maximum(np.abs(S_o), 1.0)
     assert rel.max() <= COST_RTOL, f"{label} cost rel err {rel.max():.3e} at k={rel.argmax()}"
@@ -43,7 +44,7 @@ def compare_step(ro, dbg, u0, U_next, label=""):
     np.testing.assert_allclose(u0, ro["u0"], rtol=0, atol=U_ATOL, err_msg=label)
     np.testing.assert_allclose(U_next, ro["U_next"], rtol=0, atol=U_ATOL, err_msg=label)
     assert abs(dbg["weights"].sum() - 1.0) < 1e-6
-    np.testing.assert_allclose(dbg["weights"], ro["weights"], rtol=0, atol=1e-4, err_msg=label)
+    check_weights(ro, dbg, lam, label)
     assert dbg["beta_used"] == pytest.approx(ro["beta_used"], rel=1e-5, abs=1e-6)
     assert dbg["beta_d"] == pytest.approx(ro["beta_d"], rel=1e-5, abs=1e-6)
     assert dbg["CB_star"] == pytest.approx(ro["CB_star"], rel=1e-4, abs=1e-4)
@@ -76,7 +77,8 @@ def run_pair(gpu, orc, world, steps=1, tiling=None, u_init=None):
             g.step(x, xref)
             u0, U_next = g.get_control(want_U=True)
             dbg = g.get_debug()
-            errs.append(compare_step(ro, dbg, u0, U_next, label=f"{world.name} step {i}"))
+            errs.append(compare_step(ro, dbg, u0, U_next, label=f"{world.name} step {i}",
+                                     lam=float(p["lambda"])))
             x = orc.dynamics(p, x, ro["u0"])
     return errs
 
