@@ -131,7 +131,7 @@ __device__ __forceinline__ void step_body(const CtrlDesc& D, const double* __res
   if (threadIdx.x == 0) mbar_init(&ts.mbar);
   __syncthreads();
   uint32_t phase = 0u;
-  run_tile<MODEL, NPOS, false, SGF, GRID>(D, blockIdx.x, x0, xref, smem, ts, phase);
+  run_tile_inl<MODEL, NPOS, false, SGF, GRID>(D, blockIdx.x, x0, xref, smem, ts, phase);
 }
 
 }  // namespace dbm

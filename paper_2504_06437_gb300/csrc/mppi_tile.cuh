@@ -566,10 +566,17 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
 // The batch kernels carry it, and the one-controller kernels have a form
 // with it and one without, so that controllers that do not smooth run code
 // with no trace of it.
+// The one-controller kernels inline the body (run_tile_inl), so the
+// descriptor stays the kernel's own parameter: its fields are read from the
+// parameter bank, and no store in the body can alias them.  The batch
+// kernels call it out of line (run_tile), which keeps their four-model
+// switch small.
 template <int MODEL, int NPOS, bool BATCHED, bool SGF = BATCHED, bool GRID = false>
-__device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
-                         const double* __restrict__ xrefg, char* smem, TileScratch& ts,
-                         uint32_t& mbar_phase, double* u0_out = nullptr) {
+__device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
+                                             const double* __restrict__ x0g,
+                                             const double* __restrict__ xrefg, char* smem,
+                                             TileScratch& ts, uint32_t& mbar_phase,
+                                             double* u0_out = nullptr) {
   constexpr int n = Dyn<MODEL>::n;
   const int tid = threadIdx.x, nthreads = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
@@ -895,6 +902,14 @@ __device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double*
   } else {
     final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
   }
+}
+
+template <int MODEL, int NPOS, bool BATCHED, bool SGF = BATCHED, bool GRID = false>
+__device__ __noinline__ void run_tile(const CtrlDesc& D, int tile, const double* __restrict__ x0g,
+                                      const double* __restrict__ xrefg, char* smem,
+                                      TileScratch& ts, uint32_t& mbar_phase,
+                                      double* u0_out = nullptr) {
+  run_tile_inl<MODEL, NPOS, BATCHED, SGF, GRID>(D, tile, x0g, xrefg, smem, ts, mbar_phase, u0_out);
 }
 
 }  // namespace dbm
