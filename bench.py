@@ -497,14 +497,42 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _serving_buckets(rows, pct):
+    """p50/p99 of latency, queueing and device time per request-size bucket
+    (decades of K T (7 P J + 135) FP32 operations) and per size class."""
+    edges = [0.0, 1e8, 1e9, 1e10, 1e11, float("inf")]
+    names = ["<1e8", "1e8..1e9", "1e9..1e10", "1e10..1e11", ">=1e11"]
+    out = {}
+    def summ(sel):
+        lat = np.array([r["latency"] for r in sel])
+        q = np.array([r["queue"] for r in sel])
+        d = np.array([r["device"] for r in sel])
+        return {"requests": len(sel), "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                "queue_ms": {"p50": pct(q, 50), "p99": pct(q, 99)},
+                "device_ms": {"p50": pct(d, 50), "p99": pct(d, 99)},
+                "p99_within_2ms": bool(pct(lat, 99) <= 2.0)}
+    for lo, hi, nm in zip(edges[:-1], edges[1:], names):
+        sel = [r for r in rows if lo <= r["ops"] < hi]
+        if sel:
+            out[nm] = summ(sel)
+    by_cls = {}
+    for c, nm in ((0, "small"), (1, "large")):
+        sel = [r for r in rows if r["size_class"] == c]
+        if sel:
+            by_cls[nm] = summ(sel)
+    return out, by_cls
+
+
 def run_serving(args, ws, rank, local):
     """Serving workload: robots of mixed model, K, T and obstacle count send
     closed-loop control-step requests to the continuous-batching runtime.
     First the capacity is measured with every robot resubmitting at once
     (saturation), then requests arrive with exponential think times sized to
-    a fraction of that capacity; latency is submission to completion.  The
-    plain form serves the same requests one at a time through the context
-    API (mppi_step + mppi_get_control)."""
+    a fraction of that capacity; latency is submission to completion, split
+    into time queued and the device time of the request's batch, and
+    reported per request-size bucket.  The plain form serves the same
+    requests one at a time through the context API (mppi_step +
+    mppi_get_control)."""
     import heapq
 
     import torch
@@ -515,11 +543,21 @@ def run_serving(args, ws, rank, local):
     worlds = W.serving_mix(args.robots, seed=rank)
     g = np.random.default_rng(rank)
     srv = binding.Server(len(worlds), args.pool_mb << 20, lanes=args.lanes)
-    work_of = {}
+    if args.small_ops > 0:
+        srv.set_policy(small_ops_max=args.small_ops, small_lanes=args.small_lanes,
+                       large_share=args.large_share, batch_ops_small=args.batch_ops_small,
+                       batch_ops_large=args.batch_ops_large, shortest_first=args.shortest_first,
+                       max_wait_s=args.max_wait_ms * 1e-3)
+    policy = srv.get_policy()
+
+    def ops_of(w):
+        p = w.params
+        P = int(np.asarray(p["shape"]).reshape(-1, 2).shape[0])
+        return float(p["K"]) * p["T"] * (7.0 * P * w.obstacles.shape[0] + 135.0)
 
     def run(n_req_per_robot, think_mean):
         waiting = list(range(len(worlds)))   # admission queue (memory)
-        active, x, done, lat = {}, {}, {}, []
+        active, x, done, rows = {}, {}, {}, []
         timers = []
         t_start = time.perf_counter()
         completed = 0
@@ -540,20 +578,23 @@ def run_serving(args, ws, rank, local):
                 _, r = heapq.heappop(timers)
                 w = worlds[active[r]]
                 srv.submit(r, x[r], w.reference(x[r]))
-            for (r, u0, x1, l, st) in srv.poll():
+            for d in srv.poll_timed():
+                r = d["robot"]
                 w = worlds[active[r]]
-                lat.append(l)
+                rows.append(dict(latency=d["latency"], queue=d["queue"], device=d["device"],
+                                 size_class=d["size_class"], ops=ops_of(w)))
                 completed += 1
                 total_work += int(w.params["K"]) * int(w.params["T"])
                 done[r] += 1
-                x[r] = x1[: w.n].copy()
+                x[r] = d["x1"][: w.n].copy()
                 if done[r] >= n_req_per_robot:
                     srv.leave(r)
                     del active[r]
                 else:
                     heapq.heappush(timers, (time.perf_counter() + (g.exponential(think_mean) if think_mean else 0.0), r))
         el = time.perf_counter() - t_start
-        return dict(seconds=el, requests=completed, work=total_work, lat=np.array(lat))
+        return dict(seconds=el, requests=completed, work=total_work, rows=rows,
+                    lat=np.array([r["latency"] for r in rows]))
 
     run(1, 0.0)  # warm-up
     st0 = srv.stats()
@@ -569,7 +610,6 @@ def run_serving(args, ws, rank, local):
     # plain: the same kind of requests served one at a time
     plain_lat, plain_work = [], 0
     n_plain = min(len(worlds), args.plain_robots)
-    t0 = time.perf_counter()
     for w in worlds[:n_plain]:
         with binding.Controller(w.params) as c:
             c.set_obstacles(w.obstacles)
@@ -583,7 +623,8 @@ def run_serving(args, ws, rank, local):
     plain_s = float(np.sum(plain_lat))
     if rank != 0:
         return
-    pct = lambda a, q: 1e3 * float(np.percentile(a, q))
+    pct = lambda a, q: 1e3 * float(np.percentile(a, q)) if len(a) else None
+    buckets, classes = _serving_buckets(loaded["rows"], pct)
     line = {"metric": METRIC + " and p50/p99 step latency (serving)",
             "value": loaded["work"] / loaded["seconds"], "unit": UNIT, "n_gpus": ws,
             "steps": loaded["requests"], "warmup": len(worlds),
@@ -593,9 +634,12 @@ def run_serving(args, ws, rank, local):
             "config": {"workload": f"serving_mix: {len(worlds)} robots, half unicycle half planar quadrotor, "
                                    "K log-uniform 512..32768, T 20..100, 5..500 obstacles",
                        "requests_per_robot": args.serve_steps, "lanes": args.lanes,
+                       "policy": policy,
                        "pool_mb": args.pool_mb, "offered_load": f"{args.load:.2f} of measured capacity",
                        "arrivals": "closed loop, exponential think time after each reply"},
             "latency_ms": {"p50": pct(loaded["lat"], 50), "p99": pct(loaded["lat"], 99)},
+            "latency_by_request_ops": buckets,
+            "latency_by_size_class": classes,
             "capacity": {"value": cap["work"] / cap["seconds"], "unit": UNIT,
                          "requests_per_s": cap_rps,
                          "latency_ms": {"p50": pct(cap["lat"], 50), "p99": pct(cap["lat"], 99)},
@@ -607,6 +651,7 @@ def run_serving(args, ws, rank, local):
                       "requests": len(plain_lat),
                       "latency_ms": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99)}},
             "serving_over_plain": (cap["work"] / cap["seconds"]) / (plain_work / plain_s),
+            "gpu_launches": int(st2["batches"] - st1["batches"]),
             "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -629,7 +674,15 @@ def main():
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--robots", type=int, default=1000)
     ap.add_argument("--serve-steps", type=int, default=10)
-    ap.add_argument("--lanes", type=int, default=2)
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--small-ops", type=float, default=2e9,
+                    help="serving: requests of at most this many FP32 operations are small (0: one class)")
+    ap.add_argument("--small-lanes", type=int, default=3)
+    ap.add_argument("--large-share", type=float, default=0.75)
+    ap.add_argument("--batch-ops-small", type=float, default=4e9)
+    ap.add_argument("--batch-ops-large", type=float, default=5e10)
+    ap.add_argument("--shortest-first", type=int, default=1)
+    ap.add_argument("--max-wait-ms", type=float, default=50.0)
     ap.add_argument("--pool-mb", type=int, default=2048)
     ap.add_argument("--load", type=float, default=0.5)
     ap.add_argument("--plain-robots", type=int, default=100)

@@ -400,15 +400,60 @@ int mppi_batch_destroy(mppi_batch* b);
  * memory) and keep their warm-start sequence, generator counter, exploration
  * rate and barrier state on the device.  A scheduler thread keeps up to
  * `lanes` batched steps in flight, each on its own stream; when a lane is
- * free it launches one persistent batch holding every queued request, so
- * requests that arrive while others run are served by the next batch and
- * the batches overlap on the device.  Each result equals, bit for bit, the
- * robot's result alone through a context with the same launch shape.  Not
- * part of the paper. */
+ * free it launches one persistent batch of queued requests, so requests that
+ * arrive while others run are served by the next batch and the batches
+ * overlap on the device.  Under a size-class policy (mppi_server_set_policy)
+ * small and large requests have their own queues and lanes, batches are
+ * bounded by work, and the large-request kernels leave part of the GPU to
+ * the small ones.  Each result equals, bit for bit, the robot's result alone
+ * through a context with the same launch shape.  Not part of the paper. */
 typedef struct mppi_server mppi_server;
 
+/* Scheduling policy of a server.  The work of a request is
+ * K T (7 P J + 135) FP32 operations (its samples, steps, shape points and
+ * obstacles).
+ *   small_ops_max    requests of at most this work are small, the rest
+ *                    large; 0 = one class (every lane serves one queue).
+ *   small_lanes      lanes that serve the small class (the others serve the
+ *                    large class), at least 1 and at most lanes - 1; used
+ *                    when small_ops_max > 0 and lanes >= 2.
+ *   large_share      in (0, 1]: the large-class kernels use at most this
+ *                    fraction of the CTAs the GPU holds at once, so that the
+ *                    rest of the SMs stay free for small requests.
+ *   batch_ops_small, batch_ops_large
+ *                    work cap of one batch of each class (requests are taken
+ *                    in queue order up to the cap; a request above it goes
+ *                    alone); 0 = no cap.
+ *   shortest_first   0: each class's queue is served oldest first; 1: least
+ *                    work first, except that requests queued longer than
+ *                    max_wait_s go first, oldest first (0 = no such limit).
+ *   max_wait_s       see shortest_first. */
+typedef struct {
+  double small_ops_max;
+  int32_t small_lanes;
+  int32_t shortest_first;
+  double large_share;
+  double batch_ops_small, batch_ops_large;
+  double max_wait_s;
+} mppi_server_policy;
+
+/* A server of at most max_robots robots whose state lives in a pool of
+ * pool_bytes, with `lanes` (1..8) launch lanes, one class of requests and
+ * no work caps until a policy is set.  Errors: MPPI_EINVAL, MPPI_ENOMEM,
+ * MPPI_ECUDA. */
 int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes,
                        mppi_server** out);
+
+/* Set the scheduling policy (copied).  Only while no request is queued or
+ * in flight (MPPI_ESTATE otherwise).  Errors: MPPI_EINVAL (negative or
+ * non-finite work values, large_share outside (0, 1], small_lanes < 1,
+ * shortest_first not 0 or 1, max_wait_s negative or non-finite). */
+int mppi_server_set_policy(mppi_server* s, const mppi_server_policy* pol);
+
+/* The policy in force and, if lane_classes is not NULL, the class each lane
+ * serves (lanes entries: 0 small or the only class, 1 large). */
+int mppi_server_get_policy(mppi_server* s, mppi_server_policy* pol,
+                           int32_t* lane_classes);
 
 /* Admit a robot (parameters, initial sequence or NULL, obstacle set).
  * MPPI_ENOMEM: no free slot or no room in the pool now (retry after others
@@ -427,9 +472,19 @@ int mppi_server_submit(mppi_server* s, int32_t robot, const double* x0,
 
 /* Up to max completed requests, oldest first: robot ids, u0 (2 each), the
  * model-predicted next state (6 each), latency from submission in seconds,
- * status (MPPI_OK or the error of the launch).  *n receives the count. */
+ * status (MPPI_OK or the error of the launch).  *n receives the count.
+ * Any output pointer but n may be NULL. */
 int mppi_server_poll(mppi_server* s, int32_t max, int32_t* robots, double* u0s,
                      double* x1s, double* latency_s, int32_t* status, int32_t* n);
+
+/* The same, with the latency split: queue_s = submission to the launch of
+ * the request's batch (host clock), device_s = that batch's time on the GPU
+ * from its copy-in to its copy-out (CUDA events), size_class = 0 small (or
+ * the only class), 1 large. */
+int mppi_server_poll_timed(mppi_server* s, int32_t max, int32_t* robots, double* u0s,
+                           double* x1s, double* latency_s, double* queue_s,
+                           double* device_s, int32_t* size_class, int32_t* status,
+                           int32_t* n);
 
 /* Counters: batches launched, requests completed, requests queued or in
  * flight, free pool bytes. */

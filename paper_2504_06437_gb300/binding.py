@@ -112,6 +112,13 @@ class BatchPolicy(C.Structure):
                 ("positions_per_thread", C.c_int32 * NUM_MODELS)]
 
 
+class ServerPolicy(C.Structure):
+    _fields_ = [("small_ops_max", C.c_double), ("small_lanes", C.c_int32),
+                ("shortest_first", C.c_int32), ("large_share", C.c_double),
+                ("batch_ops_small", C.c_double), ("batch_ops_large", C.c_double),
+                ("max_wait_s", C.c_double)]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 
@@ -173,6 +180,11 @@ def load():
     lib.mppi_server_submit.argtypes = [vp, C.c_int32, _dp, _dp]
     lib.mppi_server_poll.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), _dp, _dp, _dp,
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.mppi_server_poll_timed.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), _dp, _dp, _dp, _dp,
+                                           _dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32)]
+    lib.mppi_server_set_policy.argtypes = [vp, C.POINTER(ServerPolicy)]
+    lib.mppi_server_get_policy.argtypes = [vp, C.POINTER(ServerPolicy), C.POINTER(C.c_int32)]
     lib.mppi_server_stats.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
     lib.mppi_server_destroy.argtypes = [vp]
@@ -529,7 +541,11 @@ class Server:
         self._u = np.zeros((self._buf, 2))
         self._x = np.zeros((self._buf, 6))
         self._l = np.zeros(self._buf)
+        self._q = np.zeros(self._buf)
+        self._d = np.zeros(self._buf)
+        self._c = np.zeros(self._buf, dtype=np.int32)
         self._s = np.zeros(self._buf, dtype=np.int32)
+        self.lanes = int(lanes)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -581,6 +597,37 @@ class Server:
         k = n.value
         return [(int(self._r[i]), self._u[i].copy(), self._x[i].copy(), float(self._l[i]),
                  int(self._s[i])) for i in range(k)]
+
+    def poll_timed(self):
+        """Completed requests as dicts: robot, u0, x1, latency, queue and
+        device seconds, size class (0 small or the only class, 1 large),
+        status."""
+        n = C.c_int32()
+        i32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(load().mppi_server_poll_timed(self.h, self._buf, i32(self._r), _ptr(self._u),
+                                             _ptr(self._x), _ptr(self._l), _ptr(self._q),
+                                             _ptr(self._d), i32(self._c), i32(self._s),
+                                             C.byref(n)))
+        return [dict(robot=int(self._r[i]), u0=self._u[i].copy(), x1=self._x[i].copy(),
+                     latency=float(self._l[i]), queue=float(self._q[i]), device=float(self._d[i]),
+                     size_class=int(self._c[i]), status=int(self._s[i])) for i in range(n.value)]
+
+    def set_policy(self, small_ops_max: float, small_lanes: int = 1, large_share: float = 0.75,
+                   batch_ops_small: float = 0.0, batch_ops_large: float = 0.0,
+                   shortest_first: bool = False, max_wait_s: float = 0.0):
+        pol = ServerPolicy(float(small_ops_max), int(small_lanes), int(bool(shortest_first)),
+                           float(large_share), float(batch_ops_small), float(batch_ops_large),
+                           float(max_wait_s))
+        _check(load().mppi_server_set_policy(self.h, C.byref(pol)))
+
+    def get_policy(self) -> dict:
+        pol = ServerPolicy()
+        cls = (C.c_int32 * self.lanes)()
+        _check(load().mppi_server_get_policy(self.h, C.byref(pol), cls))
+        return dict(small_ops_max=pol.small_ops_max, small_lanes=pol.small_lanes,
+                    shortest_first=bool(pol.shortest_first), large_share=pol.large_share,
+                    batch_ops_small=pol.batch_ops_small, batch_ops_large=pol.batch_ops_large,
+                    max_wait_s=pol.max_wait_s, lane_classes=list(cls))
 
     def stats(self) -> dict:
         b, r, f = C.c_uint64(), C.c_uint64(), C.c_uint64()

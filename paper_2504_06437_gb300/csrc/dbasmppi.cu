@@ -1275,6 +1275,10 @@ struct BatchLane {
   std::vector<int> graph_key;  // stepped slots the graph was captured for
   size_t graph_bytes = 0;
   int graph_smem = 0, graph_grid = 0;
+  // buffers outgrown by a larger step, freed with the lane: cudaFree and
+  // cudaFreeHost wait for the whole device, which would stall a scheduler
+  // that keeps other lanes' work in flight
+  std::vector<void*> retired_host, retired_dev;
 };
 
 struct mppi_batch {
@@ -1338,7 +1342,45 @@ void free_lane(BatchLane& L) {
   cudaFree(L.d_stage);
   cudaFreeHost(L.h_out);
   cudaFree(L.d_out);
+  for (void* p : L.retired_host) cudaFreeHost(p);
+  for (void* p : L.retired_dev) cudaFree(p);
   L = BatchLane();
+}
+
+// Make room for a step of `bytes` of staging and n outputs; outgrown buffers
+// are retired, not freed (see BatchLane).
+int lane_reserve(BatchLane& L, size_t bytes, int n) {
+  if (bytes > L.stage_cap) {
+    drop_lane_graph(L);
+    if (L.h_stage) L.retired_host.push_back(L.h_stage);
+    if (L.d_stage) L.retired_dev.push_back(L.d_stage);
+    L.h_stage = nullptr;
+    L.d_stage = nullptr;
+    size_t cap = std::max(bytes, (size_t)1 << 16) * 2;
+    if (cudaMallocHost((void**)&L.h_stage, cap) != cudaSuccess ||
+        cudaMalloc((void**)&L.d_stage, cap) != cudaSuccess) {
+      cudaGetLastError();
+      L.stage_cap = 0;
+      return fail(MPPI_ENOMEM, "staging allocation failed");
+    }
+    L.stage_cap = cap;
+  }
+  if (n > L.out_cap) {
+    drop_lane_graph(L);
+    if (L.h_out) L.retired_host.push_back(L.h_out);
+    if (L.d_out) L.retired_dev.push_back(L.d_out);
+    L.h_out = nullptr;
+    L.d_out = nullptr;
+    int cap = std::max(n, 64) * 2;
+    if (cudaMallocHost((void**)&L.h_out, sizeof(double) * 8 * cap) != cudaSuccess ||
+        cudaMalloc((void**)&L.d_out, sizeof(double) * 8 * cap) != cudaSuccess) {
+      cudaGetLastError();
+      L.out_cap = 0;
+      return fail(MPPI_ENOMEM, "output allocation failed");
+    }
+    L.out_cap = cap;
+  }
+  return MPPI_OK;
 }
 
 // Device bytes of one slot (laid out in this order by slot_layout).
@@ -1598,9 +1640,12 @@ namespace {
 
 // One batched step of the listed slots on lane L and stream st: pack, copy
 // in, launch, copy out; graph replay when allowed and the composition is the
-// one captured.  Slot bookkeeping must not change concurrently.
+// one captured.  Slot bookkeeping must not change concurrently.  share < 1
+// caps the persistent kernel's CTAs at that fraction of the resident CTAs
+// the GPU holds (the serving runtime leaves the rest of the SMs to its other
+// size class); results do not depend on it.
 int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, const double* x0s,
-              const double* const* xrefs, cudaStream_t st, bool allow_graph) {
+              const double* const* xrefs, cudaStream_t st, bool allow_graph, double share = 1.0) {
   size_t n_items = 0, n_in = 0;
   int smem = 0;
   std::vector<int> order(n);
@@ -1620,34 +1665,7 @@ int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, cons
   const size_t inputs_off = (head + 15) & ~(size_t)15;
   const size_t bytes = inputs_off + sizeof(double) * n_in;
   if (L.last) CK(cudaStreamSynchronize(L.last));
-  if (bytes > L.stage_cap) {
-    drop_lane_graph(L);
-    cudaFreeHost(L.h_stage);
-    cudaFree(L.d_stage);
-    L.h_stage = nullptr;
-    L.d_stage = nullptr;
-    size_t cap = std::max(bytes, (size_t)1 << 16) * 2;
-    if (cudaMallocHost((void**)&L.h_stage, cap) != cudaSuccess ||
-        cudaMalloc((void**)&L.d_stage, cap) != cudaSuccess) {
-      cudaGetLastError();
-      L.stage_cap = 0;
-      return fail(MPPI_ENOMEM, "staging allocation failed");
-    }
-    L.stage_cap = cap;
-  }
-  if (n > L.out_cap) {
-    drop_lane_graph(L);
-    cudaFreeHost(L.h_out);
-    cudaFree(L.d_out);
-    int cap = std::max(n, 64) * 2;
-    if (cudaMallocHost((void**)&L.h_out, sizeof(double) * 8 * cap) != cudaSuccess ||
-        cudaMalloc((void**)&L.d_out, sizeof(double) * 8 * cap) != cudaSuccess) {
-      cudaGetLastError();
-      L.out_cap = 0;
-      return fail(MPPI_ENOMEM, "output allocation failed");
-    }
-    L.out_cap = cap;
-  }
+  if (int rc = lane_reserve(L, bytes, n)) return rc;
   // pack: header, step table, longest-first work items, inputs
   BatchHdr* hdr = (BatchHdr*)L.h_stage;
   StepEntry* steps = (StepEntry*)(L.h_stage + sizeof(BatchHdr));
@@ -1691,7 +1709,8 @@ int lane_step(mppi_batch* b, BatchLane& L, const int32_t* slots, int32_t n, cons
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchThreads, smem));
   if (occ < 1) return fail(MPPI_EINVAL, "batch needs %d bytes of shared memory per CTA", smem);
-  const int grid = (int)std::min<size_t>((size_t)num_sms() * occ, n_items);
+  int grid = (int)std::min<size_t>((size_t)num_sms() * occ, n_items);
+  if (share < 1.0) grid = std::max(1, std::min(grid, (int)(share * num_sms() * occ)));
   std::vector<int> key(slots, slots + n);
   const bool same = allow_graph && L.gexec && key == L.graph_key && bytes == L.graph_bytes &&
                     smem == L.graph_smem && grid == L.graph_grid && st == L.last;
@@ -1931,28 +1950,42 @@ int mppi_batch_autotune(const mppi_params* ps, const double* const* cxcyrs, cons
 // Serving runtime: continuous batching of control-step requests from many
 // robots.  Robots join by taking a slot of the device pool (admission by
 // memory); their warm-start sequence, generator counter, exploration rate
-// and barrier state stay on the device between requests.  A scheduler thread
-// keeps up to `lanes` batched steps in flight, each on its own stream: when a
-// lane is free it launches one persistent batch holding every request queued
-// so far, so requests that arrive while others run join the next batch and
-// the batches overlap on the device.  Completions carry u*_0, the model's
-// prediction of the next state and the latency from submission.
+// and barrier state stay on the device between requests.  Requests are sorted
+// by size into two classes, each with its own queue and lanes: a lane is one
+// batched step in flight on its own stream.  When a lane is free it launches
+// one persistent batch of the requests queued in its class, oldest first, up
+// to the class's work cap, so requests that arrive while others run join the
+// next batch and the batches of both classes overlap on the device.  The
+// large-request lanes cap their kernels' CTAs at a share of the GPU, which
+// leaves SMs free for the small requests: a small request does not wait for
+// a running batch of large ones.  Completions carry u*_0, the model's
+// prediction of the next state, the latency from submission, and its split
+// into time queued (submission to launch) and the batch's device time.
 
 namespace {
 
 struct ServerReq {
   int robot;
+  int cls;                   // size class: 0 small, 1 large
+  double ops;                // work estimate (FP32 operations)
   double x0[6];
   std::vector<double> xref;  // empty: goal repeated
-  std::chrono::steady_clock::time_point t0;
+  std::chrono::steady_clock::time_point t0, t_launch;
 };
 
 struct ServerDone {
   int robot;
   double out[8];  // u0[2], x1[6]
-  double latency;
+  double latency, queue, device;
+  int cls;
   int status;
 };
+
+// Work of one step of a slot: K T (7 P J + 135) FP32 operations (the
+// barrier's pairs dominate), the measure the size classes and caps use.
+double slot_ops(const BatchSlot& s) {
+  return (double)s.p.K * s.p.T * (7.0 * s.p.n_shape * s.J + 135.0);
+}
 
 }  // namespace
 
@@ -1960,14 +1993,18 @@ struct mppi_server {
   mppi_batch* b = nullptr;
   int max_robots = 0;
   std::vector<BatchLane> lanes;
+  std::vector<int> lane_cls;  // class a lane serves
   std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> events;
+  std::vector<cudaEvent_t> ev_start, events;  // per lane: launch and completion
   std::vector<std::vector<ServerReq>> inflight;
   std::vector<char> lane_busy;
-  std::mutex mu;  // queue, completions, robot flags and the slot bookkeeping
-  std::deque<ServerReq> queue;
+  std::mutex mu;       // queues, completions, robot flags and the policy
+  std::mutex slot_mu;  // the pool's slot bookkeeping (join, leave), apart from the
+                       // scheduler so that a join's uploads never stall a launch
+  std::deque<ServerReq> queue[2];
   std::deque<ServerDone> done;
   std::vector<char> joined, busy;
+  mppi_server_policy pol;
   std::thread worker;
   std::atomic<bool> stop{false};
   std::atomic<unsigned long long> batches{0}, requests{0};
@@ -1977,6 +2014,16 @@ struct mppi_server {
 };
 
 namespace {
+
+// Lane roles under a policy: with small_ops_max > 0 and two or more lanes,
+// the first small_lanes serve the small class and the rest the large class;
+// otherwise every lane serves one queue (class 0).
+void assign_lanes(mppi_server* sv) {
+  const int n = (int)sv->lanes.size();
+  const bool classes = sv->pol.small_ops_max > 0 && n >= 2;
+  int ns = classes ? std::min(std::max(sv->pol.small_lanes, 1), n - 1) : n;
+  for (int i = 0; i < n; ++i) sv->lane_cls[i] = i < ns ? 0 : 1;
+}
 
 void server_loop(mppi_server* sv) {
   // a new host thread starts on device 0: take the server's device, where
@@ -1993,6 +2040,11 @@ void server_loop(mppi_server* sv) {
       cudaError_t q = cudaEventQuery(sv->events[i]);
       if (q == cudaErrorNotReady) continue;
       const auto now = std::chrono::steady_clock::now();
+      float dev_ms = 0.0f;
+      if (q == cudaSuccess && cudaEventElapsedTime(&dev_ms, sv->ev_start[i], sv->events[i]) != cudaSuccess) {
+        cudaGetLastError();
+        dev_ms = 0.0f;
+      }
       std::lock_guard<std::mutex> g(sv->mu);
       const double* out = sv->lanes[i].h_out;
       for (size_t j = 0; j < sv->inflight[i].size(); ++j) {
@@ -2001,6 +2053,9 @@ void server_loop(mppi_server* sv) {
         d.robot = r.robot;
         for (int k = 0; k < 8; ++k) d.out[k] = q == cudaSuccess ? out[8 * j + k] : NAN;
         d.latency = std::chrono::duration<double>(now - r.t0).count();
+        d.queue = std::chrono::duration<double>(r.t_launch - r.t0).count();
+        d.device = 1e-3 * dev_ms;
+        d.cls = r.cls;
         d.status = q == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
         sv->done.push_back(d);
         sv->busy[r.robot] = 0;
@@ -2013,14 +2068,44 @@ void server_loop(mppi_server* sv) {
     }
     for (size_t i = 0; i < sv->lanes.size(); ++i) {
       if (sv->lane_busy[i]) continue;
-      std::lock_guard<std::mutex> g(sv->mu);
-      if (sv->queue.empty()) break;
-      std::vector<ServerReq>& batch = sv->inflight[i];
-      batch.clear();
-      while (!sv->queue.empty()) {
-        batch.push_back(std::move(sv->queue.front()));
-        sv->queue.pop_front();
+      std::vector<ServerReq>& batch = sv->inflight[i];  // only this thread touches it
+      double share = 1.0;
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        const int c = sv->lane_cls[i];
+        std::deque<ServerReq>& qu = sv->queue[c];
+        if (qu.empty()) continue;
+        // the oldest requests of the class, up to the class's work cap (a
+        // request above the cap goes alone)
+        const double cap = c == 0 ? sv->pol.batch_ops_small : sv->pol.batch_ops_large;
+        batch.clear();
+        double work = 0.0;
+        const auto t_launch = std::chrono::steady_clock::now();
+        if (sv->pol.shortest_first) {
+          // requests queued past the age limit first (oldest first), then
+          // the least work first; stable, so equal work keeps queue order
+          std::stable_sort(qu.begin(), qu.end(), [&](const ServerReq& a, const ServerReq& b2) {
+            const double lim = sv->pol.max_wait_s;
+            const bool oa = lim > 0 && std::chrono::duration<double>(t_launch - a.t0).count() > lim;
+            const bool ob = lim > 0 && std::chrono::duration<double>(t_launch - b2.t0).count() > lim;
+            if (oa != ob) return oa;
+            if (oa) return a.t0 < b2.t0;
+            return a.ops < b2.ops;
+          });
+        }
+        while (!qu.empty() && (batch.empty() || cap <= 0 || work + qu.front().ops <= cap)) {
+          work += qu.front().ops;
+          batch.push_back(std::move(qu.front()));
+          batch.back().t_launch = t_launch;
+          qu.pop_front();
+        }
+        // the large class's kernels leave the small class its share of the
+        // SMs whenever the small class has lanes of its own
+        bool shared = false;
+        for (size_t k = 0; k < sv->lanes.size(); ++k) shared = shared || sv->lane_cls[k] != c;
+        share = (c == 1 && shared) ? sv->pol.large_share : 1.0;
       }
+      // pack and launch outside the lock: submissions and polls go on
       const int n = (int)batch.size();
       slots.resize(n);
       x0s.assign((size_t)n * 6, 0.0);
@@ -2030,13 +2115,18 @@ void server_loop(mppi_server* sv) {
         memcpy(&x0s[(size_t)j * 6], batch[j].x0, sizeof(double) * 6);
         xr[j] = batch[j].xref.empty() ? nullptr : batch[j].xref.data();
       }
-      int rc = dev_ok ? lane_step(sv->b, sv->lanes[i], slots.data(), n, x0s.data(), xr.data(),
-                                  sv->streams[i], false)
-                      : fail(MPPI_ECUDA, "cudaSetDevice(%d) failed in the scheduler thread",
-                             sv->device);
-      if (rc == MPPI_OK) rc = cudaEventRecord(sv->events[i], sv->streams[i]) == cudaSuccess
-                                  ? MPPI_OK : MPPI_ECUDA;
+      int rc = MPPI_OK;
+      if (!dev_ok)
+        rc = fail(MPPI_ECUDA, "cudaSetDevice(%d) failed in the scheduler thread", sv->device);
+      if (rc == MPPI_OK && cudaEventRecord(sv->ev_start[i], sv->streams[i]) != cudaSuccess)
+        rc = fail(MPPI_ECUDA, "event record failed");
+      if (rc == MPPI_OK)
+        rc = lane_step(sv->b, sv->lanes[i], slots.data(), n, x0s.data(), xr.data(), sv->streams[i],
+                       false, share);
+      if (rc == MPPI_OK && cudaEventRecord(sv->events[i], sv->streams[i]) != cudaSuccess)
+        rc = fail(MPPI_ECUDA, "event record failed");
       if (rc != MPPI_OK) {
+        std::lock_guard<std::mutex> g(sv->mu);
         snprintf(sv->err, sizeof(sv->err), "%s", g_err);
         const auto now = std::chrono::steady_clock::now();
         for (const ServerReq& r : batch) {
@@ -2044,6 +2134,9 @@ void server_loop(mppi_server* sv) {
           d.robot = r.robot;
           for (int k = 0; k < 8; ++k) d.out[k] = NAN;
           d.latency = std::chrono::duration<double>(now - r.t0).count();
+          d.queue = d.latency;
+          d.device = 0.0;
+          d.cls = r.cls;
           d.status = rc;
           sv->done.push_back(d);
           sv->busy[r.robot] = 0;
@@ -2081,15 +2174,31 @@ int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes, mpp
   }
   sv->max_robots = max_robots;
   sv->lanes.resize(lanes);
-  sv->streams.resize(lanes);
-  sv->events.resize(lanes);
+  sv->lane_cls.assign(lanes, 0);
+  sv->streams.assign(lanes, nullptr);
+  sv->ev_start.assign(lanes, nullptr);
+  sv->events.assign(lanes, nullptr);
   sv->inflight.resize(lanes);
   sv->lane_busy.assign(lanes, 0);
   sv->joined.assign(max_robots, 0);
   sv->busy.assign(max_robots, 0);
+  sv->pol = mppi_server_policy{0.0, 1, 0, 0.75, 0.0, 0.0, 0.0};  // one class, oldest first
+  assign_lanes(sv);
+  // staging for a step of every robot at once (step table, inputs, a
+  // generous work list), made now so that the scheduler never has to grow it
+  const size_t stage0 = std::min<size_t>((size_t)64 << 20, ((size_t)1 << 20) + (size_t)max_robots * (16u << 10));
   for (int i = 0; i < lanes; ++i) {
-    if (cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sv->events[i], cudaEventDisableTiming) != cudaSuccess) {
+    if (lane_reserve(sv->lanes[i], stage0, max_robots) != MPPI_OK ||
+        cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&sv->ev_start[i]) != cudaSuccess ||
+        cudaEventCreate(&sv->events[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int k = 0; k <= i; ++k) {
+        free_lane(sv->lanes[k]);
+        if (sv->ev_start[k]) cudaEventDestroy(sv->ev_start[k]);
+        if (sv->events[k]) cudaEventDestroy(sv->events[k]);
+        if (sv->streams[k]) cudaStreamDestroy(sv->streams[k]);
+      }
       mppi_batch_destroy(sv->b);
       delete sv;
       return fail(MPPI_ECUDA, "stream/event creation failed");
@@ -2100,13 +2209,47 @@ int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes, mpp
   return MPPI_OK;
 }
 
+int mppi_server_set_policy(mppi_server* sv, const mppi_server_policy* pol) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  if (!pol) return fail(MPPI_EINVAL, "policy is NULL");
+  if (!std::isfinite(pol->small_ops_max) || pol->small_ops_max < 0 ||
+      !std::isfinite(pol->batch_ops_small) || pol->batch_ops_small < 0 ||
+      !std::isfinite(pol->batch_ops_large) || pol->batch_ops_large < 0)
+    return fail(MPPI_EINVAL, "work thresholds must be finite and >= 0");
+  if (!(pol->large_share > 0.0 && pol->large_share <= 1.0))
+    return fail(MPPI_EINVAL, "large_share must be in (0, 1]");
+  if (pol->small_lanes < 1) return fail(MPPI_EINVAL, "small_lanes must be >= 1");
+  if (pol->shortest_first != 0 && pol->shortest_first != 1)
+    return fail(MPPI_EINVAL, "shortest_first must be 0 or 1");
+  if (!std::isfinite(pol->max_wait_s) || pol->max_wait_s < 0)
+    return fail(MPPI_EINVAL, "max_wait_s must be finite and >= 0");
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (sv->n_inflight.load() != 0)
+    return fail(MPPI_ESTATE, "requests are queued or in flight: set the policy while idle");
+  sv->pol = *pol;
+  assign_lanes(sv);
+  return MPPI_OK;
+}
+
+int mppi_server_get_policy(mppi_server* sv, mppi_server_policy* pol, int32_t* lane_classes) {
+  if (!sv) return fail(MPPI_ESTATE, "server is NULL");
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (pol) *pol = sv->pol;
+  if (lane_classes)
+    for (size_t i = 0; i < sv->lane_cls.size(); ++i) lane_classes[i] = sv->lane_cls[i];
+  return MPPI_OK;
+}
+
 int mppi_server_join(mppi_server* sv, const mppi_params* p, const double* u_init,
                      const double* cxcyr, int32_t J, int32_t* robot) {
   if (!sv) return fail(MPPI_ESTATE, "server is NULL");
-  std::lock_guard<std::mutex> g(sv->mu);
+  if (!robot) return fail(MPPI_EINVAL, "robot is NULL");
+  std::lock_guard<std::mutex> gs(sv->slot_mu);
   int32_t slot = -1;
+  // a free slot is read by no launch, so the scheduler runs on meanwhile
   int rc = mppi_batch_add(sv->b, p, u_init, nullptr, cxcyr, J, &slot);
   if (rc) return rc;
+  std::lock_guard<std::mutex> g(sv->mu);
   sv->joined[slot] = 1;
   sv->busy[slot] = 0;
   *robot = slot;
@@ -2115,14 +2258,15 @@ int mppi_server_join(mppi_server* sv, const mppi_params* p, const double* u_init
 
 int mppi_server_leave(mppi_server* sv, int32_t robot) {
   if (!sv) return fail(MPPI_ESTATE, "server is NULL");
-  std::lock_guard<std::mutex> g(sv->mu);
-  if (robot < 0 || robot >= sv->max_robots || !sv->joined[robot])
-    return fail(MPPI_EINVAL, "robot %d has not joined", robot);
-  if (sv->busy[robot]) return fail(MPPI_ESTATE, "robot %d has a request in flight", robot);
-  int rc = mppi_batch_remove(sv->b, robot);
-  if (rc) return rc;
-  sv->joined[robot] = 0;
-  return MPPI_OK;
+  std::lock_guard<std::mutex> gs(sv->slot_mu);
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    if (robot < 0 || robot >= sv->max_robots || !sv->joined[robot])
+      return fail(MPPI_EINVAL, "robot %d has not joined", robot);
+    if (sv->busy[robot]) return fail(MPPI_ESTATE, "robot %d has a request in flight", robot);
+    sv->joined[robot] = 0;  // no request can be queued for it from here on
+  }
+  return mppi_batch_remove(sv->b, robot);
 }
 
 int mppi_server_submit(mppi_server* sv, int32_t robot, const double* x0, const double* xref) {
@@ -2142,14 +2286,19 @@ int mppi_server_submit(mppi_server* sv, int32_t robot, const double* x0, const d
     r.xref.assign(xref, xref + (size_t)(s.p.T + 1) * s.n);
     if (!finite_all(r.xref.data(), (int)r.xref.size())) return fail(MPPI_EINVAL, "xref is not finite");
   }
+  r.ops = slot_ops(s);
+  bool two = false;
+  for (int c : sv->lane_cls) two = two || c == 1;
+  r.cls = (two && r.ops > sv->pol.small_ops_max) ? 1 : 0;
   sv->busy[robot] = 1;
   sv->n_inflight++;
-  sv->queue.push_back(std::move(r));
+  sv->queue[r.cls].push_back(std::move(r));
   return MPPI_OK;
 }
 
-int mppi_server_poll(mppi_server* sv, int32_t max, int32_t* robots, double* u0s, double* x1s,
-                     double* latency_s, int32_t* status, int32_t* n_out) {
+int mppi_server_poll_timed(mppi_server* sv, int32_t max, int32_t* robots, double* u0s, double* x1s,
+                           double* latency_s, double* queue_s, double* device_s,
+                           int32_t* size_class, int32_t* status, int32_t* n_out) {
   if (!sv) return fail(MPPI_ESTATE, "server is NULL");
   if (!n_out) return fail(MPPI_EINVAL, "n_out is NULL");
   std::lock_guard<std::mutex> g(sv->mu);
@@ -2164,12 +2313,21 @@ int mppi_server_poll(mppi_server* sv, int32_t max, int32_t* robots, double* u0s,
     if (x1s)
       for (int k = 0; k < 6; ++k) x1s[6 * n + k] = d.out[2 + k];
     if (latency_s) latency_s[n] = d.latency;
+    if (queue_s) queue_s[n] = d.queue;
+    if (device_s) device_s[n] = d.device;
+    if (size_class) size_class[n] = d.cls;
     if (status) status[n] = d.status;
     sv->done.pop_front();
     ++n;
   }
   *n_out = n;
   return MPPI_OK;
+}
+
+int mppi_server_poll(mppi_server* sv, int32_t max, int32_t* robots, double* u0s, double* x1s,
+                     double* latency_s, int32_t* status, int32_t* n_out) {
+  return mppi_server_poll_timed(sv, max, robots, u0s, x1s, latency_s, nullptr, nullptr, nullptr,
+                                status, n_out);
 }
 
 int mppi_server_stats(mppi_server* sv, uint64_t* batches, uint64_t* requests, int32_t* pending,
@@ -2179,7 +2337,7 @@ int mppi_server_stats(mppi_server* sv, uint64_t* batches, uint64_t* requests, in
   if (requests) *requests = sv->requests.load();
   if (pending) *pending = sv->n_inflight.load();
   if (pool_free_bytes) {
-    std::lock_guard<std::mutex> g(sv->mu);
+    std::lock_guard<std::mutex> g(sv->slot_mu);
     size_t f = 0;
     for (auto& e : sv->b->free_list) f += e.second;
     *pool_free_bytes = f;
@@ -2193,6 +2351,7 @@ int mppi_server_destroy(mppi_server* sv) {
   if (sv->worker.joinable()) sv->worker.join();
   for (size_t i = 0; i < sv->lanes.size(); ++i) {
     free_lane(sv->lanes[i]);
+    cudaEventDestroy(sv->ev_start[i]);
     cudaEventDestroy(sv->events[i]);
     cudaStreamDestroy(sv->streams[i]);
   }

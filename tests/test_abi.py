@@ -71,6 +71,28 @@ def test_struct_layout_matches_header():
     assert out[-1] == C.sizeof(binding.Tiling)
 
 
+def test_server_policy_layout_matches_header():
+    """The serving policy struct: sizeof/offsetof against the ctypes mirror."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc unavailable")
+    fields = [f for f, _ in binding.ServerPolicy._fields_]
+    body = "\n".join(f'  printf("%zu\\n", offsetof(mppi_server_policy, {f}));' for f in fields)
+    prog = ("#include <stdio.h>\n#include <stddef.h>\n#include \"dbasmppi.h\"\nint main(void){\n"
+            f'  printf("%zu\\n", sizeof(mppi_server_policy));\n{body}\n  return 0;\n}}\n')
+    d = tempfile.mkdtemp()
+    try:
+        src, exe = os.path.join(d, "probe.c"), os.path.join(d, "probe")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    assert out[0] == C.sizeof(binding.ServerPolicy)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(binding.ServerPolicy, f).offset == off, f
+
+
 def _bad(cfg_over):
     p = W.base_params(W.UNICYCLE, K=64, T=10, dt=0.05, seed=0)
     p.update(x_goal=np.zeros(3))

@@ -118,3 +118,61 @@ def test_many_requests_complete(gpu):
             srv.submit(robots[0], worlds[0].x_start)
             srv.submit(robots[0], worlds[0].x_start)    # second while the first is queued
         wait_all(srv, 1)
+
+
+def test_size_classes_small_request_passes_large(gpu):
+    """Under a size-class policy a small request submitted just after a large
+    one completes first: the large class's kernel leaves part of the GPU to
+    the small class's lane, so the small request does not wait for it.  The
+    timed poll splits each latency into time queued and the batch's device
+    time, and reports the class; results stay equal, bit for bit, to the
+    same robots alone."""
+    big = W.quad2d(4, K=32768, T=100)
+    big.obstacles = np.concatenate([big.obstacles] * 12)[:480]
+    small = W.unicycle_small(4)
+    with gpu.Server(4, 1 << 30, lanes=2) as srv:
+        srv.set_policy(small_ops_max=1e9, small_lanes=1, large_share=0.75, shortest_first=True,
+                       max_wait_s=0.05)
+        pol = srv.get_policy()
+        assert pol["shortest_first"] and pol["max_wait_s"] == 0.05
+        assert pol["lane_classes"] == [0, 1]
+        rb = srv.join(big.params, big.obstacles)
+        rs = srv.join(small.params, small.obstacles)
+        srv.submit(rb, big.x_start)
+        time.sleep(0.0005)
+        srv.submit(rs, small.x_start)
+        got = []
+        t0 = time.time()
+        while len(got) < 2:
+            got += srv.poll_timed()
+            assert time.time() - t0 < 60
+        assert [d["robot"] for d in got] == [rs, rb], "the small request waited for the large one"
+        for d in got:
+            assert d["status"] == 0
+            assert d["size_class"] == (1 if d["robot"] == rb else 0)
+            assert 0.0 <= d["queue"] <= d["latency"] and 0.0 < d["device"] <= d["latency"]
+        res = {d["robot"]: d["u0"] for d in got}
+        with pytest.raises(gpu.MppiError):          # only while idle
+            srv.submit(rs, small.x_start)
+            srv.set_policy(small_ops_max=0.0)
+        got = []
+        while len(got) < 1:
+            got += srv.poll_timed()
+    for r, w in ((rb, big), (rs, small)):
+        with gpu.Batch(2, 1 << 30) as b:
+            info = b.slot_info(b.add(w.params, w.obstacles))
+        with gpu.Controller(w.params, tiling=dict(samples_per_cta=info["samples_per_cta"], threads=256,
+                                                  positions_per_thread=info["positions_per_thread"])) as c:
+            c.set_obstacles(w.obstacles)
+            c.step(w.x_start)
+            np.testing.assert_array_equal(c.get_control(), res[r])
+
+
+def test_policy_rejects_bad_values(gpu):
+    with gpu.Server(4, 64 << 20, lanes=2) as srv:
+        for bad in (dict(small_ops_max=-1.0), dict(small_ops_max=1e9, large_share=0.0),
+                    dict(small_ops_max=1e9, large_share=1.5), dict(small_ops_max=1e9, small_lanes=0),
+                    dict(small_ops_max=float("nan")), dict(small_ops_max=1e9, max_wait_s=-1.0)):
+            with pytest.raises(gpu.MppiError) as e:
+                srv.set_policy(**bad)
+            assert e.value.code == gpu.MPPI_EINVAL
