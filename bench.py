@@ -724,7 +724,8 @@ def main():
         S_, NT_, NP_ = (int(v) for v in args.tiling.split(","))
         tiling = dict(samples_per_cta=S_, threads=NT_, positions_per_thread=NP_)
     elif not args.no_autotune:
-        tiling, tune_us = binding.autotune(p, world.obstacles, iters=10)
+        # tuned the way it is timed below: each step alone after the L2 flush
+        tiling, tune_us = binding.autotune(p, world.obstacles, iters=10, flush_bytes=L2_FLUSH_BYTES)
     ctl = binding.Controller(p, tiling=tiling)
     ctl.set_obstacles(world.obstacles)
     has_grid = p.get("grid") is not None

@@ -235,6 +235,19 @@ int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int32_t J, con
                        int32_t nx, int32_t ny, double ox, double oy, double res, int32_t iters,
                        mppi_tiling* best, float* best_us);
 
+/* The same, timing each candidate's steps the way a caller that steps once
+ * per control period sees them: with flush_bytes > 0 every timed step runs
+ * alone, after a device-memory write of flush_bytes (an L2 flush when it
+ * exceeds the 129 MB L2), between its own pair of events; at least `iters`
+ * such steps, at most 40.  flush_bytes = 0 is mppi_autotune_grid (steps back
+ * to back).  The small one-wave problems rank their launch shapes
+ * differently the two ways.  Errors: as mppi_autotune_grid; MPPI_EINVAL for
+ * flush_bytes above 4 GiB, MPPI_ENOMEM if the flush buffer cannot be
+ * allocated. */
+int mppi_autotune_flush(const mppi_params* p, const double* cxcyr, int32_t J, const float* sdf,
+                        int32_t nx, int32_t ny, double ox, double oy, double res, int32_t iters,
+                        uint64_t flush_bytes, mppi_tiling* best, float* best_us);
+
 /* The launch shape in use and the number of CTAs of one step. */
 int mppi_get_tiling(mppi_ctx* c, mppi_tiling* t, int32_t* n_ctas);
 

@@ -155,6 +155,10 @@ def load():
                                        C.c_int32, C.POINTER(Tiling), C.POINTER(C.c_float)]
     lib.mppi_autotune.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.c_int32,
                                   C.POINTER(Tiling), C.POINTER(C.c_float)]
+    lib.mppi_autotune_flush.argtypes = [C.POINTER(Params), _dp, C.c_int32, C.POINTER(C.c_float),
+                                        C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                        C.c_int32, C.c_uint64, C.POINTER(Tiling),
+                                        C.POINTER(C.c_float)]
     lib.mppi_batch_create.argtypes = [C.c_int32, C.c_size_t, C.POINTER(vp)]
     lib.mppi_batch_add.argtypes = [vp, C.POINTER(Params), _dp, C.POINTER(Tiling), _dp, C.c_int32,
                                    C.POINTER(C.c_int32)]
@@ -244,24 +248,24 @@ def debug_draws(cfg: dict, S_e: float, it: int, K: int, T: int):
     return raw, du
 
 
-def autotune(cfg: dict, obstacles, iters: int = 10):
+def autotune(cfg: dict, obstacles, iters: int = 10, flush_bytes: int = 0):
     """Fastest launch shape for this problem: (tiling dict, microseconds per step).
     A grid map in cfg (``grid``, ``grid_ox``, ``grid_oy``, ``grid_res``) is
-    set on every candidate."""
+    set on every candidate.  flush_bytes > 0 times each candidate step alone
+    after a device write of that size (mppi_autotune_flush)."""
     p = make_params(cfg)
     ob = _f64(obstacles).reshape(-1, 3)
     t = Tiling()
     us = C.c_float()
     g = cfg.get("grid")
+    gp, nx, ny, gox, goy, gres = None, 0, 0, 0.0, 0.0, 0.0
     if g is not None:
         g = np.ascontiguousarray(g, dtype=np.float32)
-        _check(load().mppi_autotune_grid(
-            C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0],
-            g.ctypes.data_as(C.POINTER(C.c_float)), g.shape[1], g.shape[0], float(cfg["grid_ox"]),
-            float(cfg["grid_oy"]), float(cfg["grid_res"]), int(iters), C.byref(t), C.byref(us)))
-    else:
-        _check(load().mppi_autotune(C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0],
-                                    int(iters), C.byref(t), C.byref(us)))
+        gp, nx, ny = g.ctypes.data_as(C.POINTER(C.c_float)), g.shape[1], g.shape[0]
+        gox, goy, gres = float(cfg["grid_ox"]), float(cfg["grid_oy"]), float(cfg["grid_res"])
+    _check(load().mppi_autotune_flush(C.byref(p), _ptr(ob) if ob.size else None, ob.shape[0], gp,
+                                      nx, ny, gox, goy, gres, int(iters), int(flush_bytes),
+                                      C.byref(t), C.byref(us)))
     return dict(samples_per_cta=t.samples_per_cta, threads=t.threads,
                 positions_per_thread=t.positions_per_thread, chunk_steps=0), float(us.value)
 

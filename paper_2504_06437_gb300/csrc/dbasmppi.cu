@@ -1141,20 +1141,38 @@ extern "C" int mppi_step_static(const mppi_params* p, const double* d_obst, int3
 // candidate sees the same inputs.
 constexpr float kTuneWindowUs = 2000.0f;  // device time timed per candidate, at least
 constexpr int kTuneMaxReps = 400;
+constexpr int kTuneMaxRepsFlushed = 40;  // each flushed step also writes the flush buffer
 
 extern "C" int mppi_autotune(const mppi_params* p, const double* cxcyr, int32_t J, int32_t iters,
                              mppi_tiling* best, float* best_us) {
-  return mppi_autotune_grid(p, cxcyr, J, nullptr, 0, 0, 0.0, 0.0, 0.0, iters, best, best_us);
+  return mppi_autotune_flush(p, cxcyr, J, nullptr, 0, 0, 0.0, 0.0, 0.0, iters, 0, best, best_us);
 }
 
 extern "C" int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int32_t J,
                                   const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
                                   double res, int32_t iters, mppi_tiling* best, float* best_us) {
+  return mppi_autotune_flush(p, cxcyr, J, sdf, nx, ny, ox, oy, res, iters, 0, best, best_us);
+}
+
+extern "C" int mppi_autotune_flush(const mppi_params* p, const double* cxcyr, int32_t J,
+                                   const float* sdf, int32_t nx, int32_t ny, double ox, double oy,
+                                   double res, int32_t iters, uint64_t flush_bytes,
+                                   mppi_tiling* best, float* best_us) {
   int rc = validate(p);
   if (rc) return rc;
   if (sdf && (rc = check_grid(sdf, nx, ny, ox, oy, res))) return rc;
   if (!best) return fail(MPPI_EINVAL, "best is NULL");
+  if (flush_bytes > ((uint64_t)4 << 30)) return fail(MPPI_EINVAL, "flush_bytes above 4 GiB");
   if (iters < 1) iters = 5;
+  // with flush_bytes, each timed step runs alone after a write of that many
+  // bytes (an L2 flush when it exceeds the L2), as a caller that steps once
+  // per control period sees it
+  void* flush = nullptr;
+  if (flush_bytes && cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPPI_ENOMEM, "cudaMalloc of the %llu-byte flush buffer failed",
+                (unsigned long long)flush_bytes);
+  }
   const int sms = num_sms();
   int S_opts[32];
   for (int i = 0; i < 32; ++i) S_opts[i] = i + 1;
@@ -1199,16 +1217,30 @@ extern "C" int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int
         float ms = 0.0f;
         for (int pass = 0; pass < 2 && ok; ++pass) {
           const int k = pass == 0 ? 2 : reps;
-          cudaEventRecord(e0, c->own);
-          for (int i = 0; i < k && ok; ++i)
-            ok = mppi_step_device(c, c->d_in, c->d_in + n, nullptr) == MPPI_OK;
-          cudaEventRecord(e1, c->own);
-          ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
-          if (ok) cudaEventElapsedTime(&ms, e0, e1);
+          if (flush) {  // each step alone, after the flush, its own events
+            ms = 0.0f;
+            for (int i = 0; i < k && ok; ++i) {
+              float one = 0.0f;
+              ok = cudaMemsetAsync(flush, i & 0xff, flush_bytes, c->own) == cudaSuccess &&
+                   cudaEventRecord(e0, c->own) == cudaSuccess &&
+                   mppi_step_device(c, c->d_in, c->d_in + n, nullptr) == MPPI_OK &&
+                   cudaEventRecord(e1, c->own) == cudaSuccess &&
+                   cudaEventSynchronize(e1) == cudaSuccess &&
+                   cudaEventElapsedTime(&one, e0, e1) == cudaSuccess;
+              ms += one;
+            }
+          } else {
+            cudaEventRecord(e0, c->own);
+            for (int i = 0; i < k && ok; ++i)
+              ok = mppi_step_device(c, c->d_in, c->d_in + n, nullptr) == MPPI_OK;
+            cudaEventRecord(e1, c->own);
+            ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+            if (ok) cudaEventElapsedTime(&ms, e0, e1);
+          }
           if (pass == 0 && ok) {
             const float est_us = 1000.0f * ms / 2.0f;
             const float want = est_us > 0.0f ? kTuneWindowUs / est_us : (float)kTuneMaxReps;
-            reps = std::max(iters, std::min(kTuneMaxReps, (int)want + 1));
+            reps = std::max(iters, std::min(flush ? kTuneMaxRepsFlushed : kTuneMaxReps, (int)want + 1));
           }
         }
         mppi_destroy(c);
@@ -1225,6 +1257,7 @@ extern "C" int mppi_autotune_grid(const mppi_params* p, const double* cxcyr, int
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaFree(flush);
   delete[] x0;
   if (best_tl.samples_per_cta == 0) return fail(MPPI_ECUDA, "no launch shape ran");
   *best = best_tl;

@@ -139,6 +139,18 @@ def test_grid_rejected_without_gpu(lib, nx, ny, res, value):
     assert b"grid" in lib.mppi_last_error()
 
 
+def test_autotune_flush_bound_without_gpu(lib):
+    """mppi_autotune_flush refuses a flush write above 4 GiB before any CUDA
+    call."""
+    p = binding.make_params(_bad({}))
+    t = binding.Tiling()
+    us = C.c_float()
+    rc = lib.mppi_autotune_flush(C.byref(p), None, 0, None, 0, 0, 0.0, 0.0, 0.0, 1, 5 << 30,
+                                 C.byref(t), C.byref(us))
+    assert rc == binding.MPPI_EINVAL
+    assert b"flush" in lib.mppi_last_error()
+
+
 def test_null_handles(lib):
     assert lib.mppi_destroy(None) == binding.MPPI_OK
     assert lib.mppi_step(None, None, None, None) == binding.MPPI_ESTATE

@@ -195,8 +195,9 @@ def test_max_sizes(gpu, orc):
 
 def bench_tiling(gpu, w):
     """The launch shape bench.py times for this workload: the autotuner's
-    pick, made the same way (10 timed steps per candidate at least)."""
-    tiling, _ = gpu.autotune(w.params, w.obstacles, iters=10)
+    pick, made the same way (10 timed steps per candidate at least, each
+    alone after a 256 MB write, as the bench times them)."""
+    tiling, _ = gpu.autotune(w.params, w.obstacles, iters=10, flush_bytes=256 << 20)
     return tiling
 
 
@@ -490,6 +491,9 @@ def test_grid_autotune(gpu, orc):
     oracle."""
     w = W.ackermann_grid(2, K=512, T=20)
     tiling, us = gpu.autotune(w.params, w.obstacles, iters=3)
+    assert us > 0 and tiling["threads"] in (128, 256, 512)
+    run_pair(gpu, orc, w, steps=1, tiling=tiling)
+    tiling, us = gpu.autotune(w.params, w.obstacles, iters=3, flush_bytes=64 << 20)
     assert us > 0 and tiling["threads"] in (128, 256, 512)
     run_pair(gpu, orc, w, steps=1, tiling=tiling)
 

@@ -76,7 +76,7 @@ def test_precision_against_oracle(gpu, orc, name):
     x = w.x_start
     xref = w.reference(x)
     ro = orc.step(p, w.obstacles, x, xref, ctl)
-    tiling, _ = gpu.autotune(p, w.obstacles, iters=10)
+    tiling, _ = gpu.autotune(p, w.obstacles, iters=10, flush_bytes=256 << 20)
     with gpu.Controller(p, u_init=u_init, tiling=tiling) as g:
         g.set_obstacles(w.obstacles)
         g.step(x, xref)
