@@ -525,7 +525,9 @@ def _serving_buckets(rows, pct):
 
 def run_serving(args, ws, rank, local):
     """Serving workload: robots of mixed model, K, T and obstacle count send
-    closed-loop control-step requests to the continuous-batching runtime.
+    closed-loop control-step requests to the continuous-batching runtime
+    (by default its device queue: one resident kernel that takes requests
+    as they arrive, small ones first).
     First the capacity is measured with every robot resubmitting at once
     (saturation), then requests arrive with exponential think times sized to
     a fraction of that capacity; latency is submission to completion, split
@@ -543,11 +545,13 @@ def run_serving(args, ws, rank, local):
     worlds = W.serving_mix(args.robots, seed=rank)
     g = np.random.default_rng(rank)
     srv = binding.Server(len(worlds), args.pool_mb << 20, lanes=args.lanes)
-    if args.small_ops > 0:
+    if args.batch_ops_small is None:
+        args.batch_ops_small = 0.0 if args.device_queue else 4e9
+    if args.small_ops > 0 or args.device_queue:
         srv.set_policy(small_ops_max=args.small_ops, small_lanes=args.small_lanes,
                        large_share=args.large_share, batch_ops_small=args.batch_ops_small,
                        batch_ops_large=args.batch_ops_large, shortest_first=args.shortest_first,
-                       max_wait_s=args.max_wait_ms * 1e-3)
+                       max_wait_s=args.max_wait_ms * 1e-3, device_queue=bool(args.device_queue))
     policy = srv.get_policy()
 
     def ops_of(w):
@@ -679,10 +683,14 @@ def main():
                     help="serving: requests of at most this many FP32 operations are small (0: one class)")
     ap.add_argument("--small-lanes", type=int, default=3)
     ap.add_argument("--large-share", type=float, default=0.75)
-    ap.add_argument("--batch-ops-small", type=float, default=4e9)
+    ap.add_argument("--batch-ops-small", type=float, default=None,
+                    help="lanes: work cap of a small batch (default 4e9); device queue: cap on "
+                         "published small work (default 0, none)")
     ap.add_argument("--batch-ops-large", type=float, default=5e10)
     ap.add_argument("--shortest-first", type=int, default=1)
     ap.add_argument("--max-wait-ms", type=float, default=50.0)
+    ap.add_argument("--device-queue", type=int, default=1,
+                    help="serving: one resident kernel takes requests as they arrive (1) or lanes of batches (0)")
     ap.add_argument("--pool-mb", type=int, default=2048)
     ap.add_argument("--load", type=float, default=0.5)
     ap.add_argument("--plain-robots", type=int, default=100)

@@ -440,7 +440,23 @@ typedef struct mppi_server mppi_server;
  *   shortest_first   0: each class's queue is served oldest first; 1: least
  *                    work first, except that requests queued longer than
  *                    max_wait_s go first, oldest first (0 = no such limit).
- *   max_wait_s       see shortest_first. */
+ *   max_wait_s       see shortest_first.
+ *   device_queue     0: the lanes above.  1: one resident persistent kernel
+ *                    serves every request: the scheduler publishes each
+ *                    request's tiles into a ring in mapped host memory that
+ *                    the running kernel claims from, small requests' tiles
+ *                    first, so a request that arrives mid-flight joins the
+ *                    running kernel at the next tile boundary; the
+ *                    scheduler closes the kernel after 0.3 ms with nothing
+ *                    queued or in flight and launches it again when work
+ *                    arrives.  small_ops_max sets the classes;
+ *                    small_lanes and large_share do not apply; the batch
+ *                    caps bound each class's published, unfinished work
+ *                    (requests beyond it wait on the host), and
+ *                    shortest_first / max_wait_s order the requests so
+ *                    held.  The poll's queue time is then submission to
+ *                    publication and its device time publication to
+ *                    completion (host clock). */
 typedef struct {
   double small_ops_max;
   int32_t small_lanes;
@@ -448,6 +464,8 @@ typedef struct {
   double large_share;
   double batch_ops_small, batch_ops_large;
   double max_wait_s;
+  int32_t device_queue;
+  int32_t reserved;
 } mppi_server_policy;
 
 /* A server of at most max_robots robots whose state lives in a pool of
@@ -460,7 +478,8 @@ int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes,
 /* Set the scheduling policy (copied).  Only while no request is queued or
  * in flight (MPPI_ESTATE otherwise).  Errors: MPPI_EINVAL (negative or
  * non-finite work values, large_share outside (0, 1], small_lanes < 1,
- * shortest_first not 0 or 1, max_wait_s negative or non-finite). */
+ * shortest_first or device_queue not 0 or 1, max_wait_s negative or
+ * non-finite), MPPI_ENOMEM (the device queue's mapped rings). */
 int mppi_server_set_policy(mppi_server* s, const mppi_server_policy* pol);
 
 /* The policy in force and, if lane_classes is not NULL, the class each lane

@@ -116,7 +116,7 @@ class ServerPolicy(C.Structure):
     _fields_ = [("small_ops_max", C.c_double), ("small_lanes", C.c_int32),
                 ("shortest_first", C.c_int32), ("large_share", C.c_double),
                 ("batch_ops_small", C.c_double), ("batch_ops_large", C.c_double),
-                ("max_wait_s", C.c_double)]
+                ("max_wait_s", C.c_double), ("device_queue", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -618,10 +618,11 @@ class Server:
 
     def set_policy(self, small_ops_max: float, small_lanes: int = 1, large_share: float = 0.75,
                    batch_ops_small: float = 0.0, batch_ops_large: float = 0.0,
-                   shortest_first: bool = False, max_wait_s: float = 0.0):
+                   shortest_first: bool = False, max_wait_s: float = 0.0,
+                   device_queue: bool = False):
         pol = ServerPolicy(float(small_ops_max), int(small_lanes), int(bool(shortest_first)),
                            float(large_share), float(batch_ops_small), float(batch_ops_large),
-                           float(max_wait_s))
+                           float(max_wait_s), int(bool(device_queue)), 0)
         _check(load().mppi_server_set_policy(self.h, C.byref(pol)))
 
     def get_policy(self) -> dict:
@@ -631,7 +632,8 @@ class Server:
         return dict(small_ops_max=pol.small_ops_max, small_lanes=pol.small_lanes,
                     shortest_first=bool(pol.shortest_first), large_share=pol.large_share,
                     batch_ops_small=pol.batch_ops_small, batch_ops_large=pol.batch_ops_large,
-                    max_wait_s=pol.max_wait_s, lane_classes=list(cls))
+                    max_wait_s=pol.max_wait_s, device_queue=bool(pol.device_queue),
+                    lane_classes=list(cls))
 
     def stats(self) -> dict:
         b, r, f = C.c_uint64(), C.c_uint64(), C.c_uint64()

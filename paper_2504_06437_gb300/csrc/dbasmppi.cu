@@ -2014,6 +2014,51 @@ struct ServerDone {
   int status;
 };
 
+// A request published to the resident kernel's rings (device-queue mode).
+struct RingReq {
+  ServerReq r;
+  int rq = 0;              // request slot of the rings
+  unsigned seq = 0;        // its sequence number (done word: seq + 1)
+  int cls = 0;
+  double ops = 0.0;
+  unsigned item_begin = 0;  // its items: [item_begin, item_begin + nTiles) of its class
+  std::chrono::steady_clock::time_point t_publish;
+  bool done = false;
+};
+
+// The resident kernel's rings and the scheduler's view of them; only the
+// scheduler thread touches it after set-up.
+struct ServeState {
+  bool ready = false;
+  ServeHdr* h_hdr = nullptr;
+  ServeHdr* d_hdr = nullptr;
+  WorkItem* h_items[2] = {nullptr, nullptr};
+  WorkItem* d_items[2] = {nullptr, nullptr};
+  ServeReq* h_reqs = nullptr;
+  ServeReq* d_reqs = nullptr;
+  double* h_in = nullptr;
+  double* d_in = nullptr;
+  double* h_out = nullptr;
+  double* d_out = nullptr;
+  unsigned* h_done = nullptr;
+  unsigned* d_done = nullptr;
+  unsigned* d_next = nullptr;  // device memory: items claimed per class
+  unsigned cap_items = 0;
+  int cap_reqs = 0, in_stride = 0, max_dyn = 0;
+  unsigned pub[2] = {0, 0};  // items published per class
+  double flight_ops[2] = {0.0, 0.0};  // work published and not yet complete, per class
+  unsigned seq = 0;
+  std::chrono::steady_clock::time_point last_busy;  // last pass with work queued or in flight
+  std::vector<int> free_rq;
+  std::deque<RingReq> flight[2];  // published requests per class, in publish order
+  int n_flight = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool running = false, closing = false, failed = false;
+  int k_smem = 0;
+  bool k_all = false;
+};
+
 // Work of one step of a slot: K T (7 P J + 135) FP32 operations (the
 // barrier's pairs dominate), the measure the size classes and caps use.
 double slot_ops(const BatchSlot& s) {
@@ -2043,6 +2088,10 @@ struct mppi_server {
   std::atomic<unsigned long long> batches{0}, requests{0};
   std::atomic<int> n_inflight{0};
   int device = 0;  // the device current at mppi_server_create, where the pool lives
+  int max_slot_smem = 0;  // largest shared memory of a joined robot's tiles (never lowered)
+  bool any_all = false;   // a joined robot needs the four-model kernel (never cleared)
+  ServeState ring;        // device-queue mode
+  std::atomic<bool> dq{false};  // the policy's device_queue, read by the scheduler
   char err[512] = "";
 };
 
@@ -2058,6 +2107,302 @@ void assign_lanes(mppi_server* sv) {
   for (int i = 0; i < n; ++i) sv->lane_cls[i] = i < ns ? 0 : 1;
 }
 
+// ---- device-queue mode: the resident kernel's rings
+
+constexpr unsigned kRingItems = 1u << 21;  // items per class ring (a power of two)
+// The resident kernel's CTAs exit when the host closes the kernel, which it
+// does after kServeIdleClose with nothing queued or in flight (CTAs leaving
+// one by one would leave a running kernel with too few CTAs for the work
+// that arrives next).  On the device each idle wait is still bounded:
+// kServeIdlePolls polls kServeIdleNs apart, about 2 s, after which a CTA
+// exits on its own.
+constexpr int kServeIdlePolls = 400000;
+constexpr int kServeIdleNs = 5000;
+constexpr double kServeIdleClose = 3e-4;  // seconds
+
+template <class T>
+bool mapped_alloc(T** h, T** d, size_t n) {
+  if (cudaHostAlloc((void**)h, sizeof(T) * n, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)d, *h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  memset(*h, 0, sizeof(T) * n);
+  return true;
+}
+
+// Stop the resident kernel (if any) and release the rings.
+void ring_free(ServeState& R) {
+  if (R.running) {
+    *reinterpret_cast<volatile unsigned*>(&R.h_hdr->closed) = 1u;
+    cudaStreamSynchronize(R.stream);
+    R.running = false;
+  }
+  cudaFreeHost(R.h_hdr);
+  for (int c = 0; c < 2; ++c) cudaFreeHost(R.h_items[c]);
+  cudaFreeHost(R.h_reqs);
+  cudaFreeHost(R.h_in);
+  cudaFreeHost(R.h_out);
+  cudaFreeHost(R.h_done);
+  cudaFree(R.d_next);
+  if (R.ev) cudaEventDestroy(R.ev);
+  if (R.stream) cudaStreamDestroy(R.stream);
+  R = ServeState();
+}
+
+// Rings for up to max_robots requests in flight (one per robot).
+int ring_alloc(mppi_server* sv) {
+  ServeState& R = sv->ring;
+  if (R.ready) return MPPI_OK;
+  R.cap_items = kRingItems;
+  R.cap_reqs = sv->max_robots;
+  R.in_stride = (MPPI_MAX_T + 2) * kMaxN;
+  bool ok = mapped_alloc(&R.h_hdr, &R.d_hdr, 1) && mapped_alloc(&R.h_items[0], &R.d_items[0], R.cap_items) &&
+            mapped_alloc(&R.h_items[1], &R.d_items[1], R.cap_items) &&
+            mapped_alloc(&R.h_reqs, &R.d_reqs, (size_t)R.cap_reqs) &&
+            mapped_alloc(&R.h_in, &R.d_in, (size_t)R.cap_reqs * R.in_stride) &&
+            mapped_alloc(&R.h_out, &R.d_out, (size_t)R.cap_reqs * 8) &&
+            mapped_alloc(&R.h_done, &R.d_done, (size_t)R.cap_reqs);
+  ok = ok && cudaMalloc((void**)&R.d_next, 2 * sizeof(unsigned)) == cudaSuccess &&
+       cudaMemset(R.d_next, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&R.stream, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&R.ev, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) {
+    // dynamic shared memory the serving kernels may take beside their own
+    // static staging of the inputs
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    size_t stat = 0;
+    for (auto k : {serve_kernel, serve_kernel_all})
+      if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.sharedSizeBytes > stat)
+        stat = fa.sharedSizeBytes;
+    R.max_dyn = optin - align_up((int)stat + 64, 128);
+    ok = R.max_dyn > 0 &&
+         cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, R.max_dyn) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(serve_kernel_all, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              R.max_dyn) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    ring_free(R);
+    return fail(MPPI_ENOMEM, "device queue: allocation of its rings failed");
+  }
+  for (int i = R.cap_reqs - 1; i >= 0; --i) R.free_rq.push_back(i);
+  R.ready = true;
+  return MPPI_OK;
+}
+
+// One pass of the device-queue scheduler: completions, publication of
+// queued requests, and a launch of the resident kernel when work is
+// published and none runs.  Returns whether anything happened.
+bool ring_step(mppi_server* sv, bool dev_ok) {
+  ServeState& R = sv->ring;
+  bool did = false;
+  if (R.running) {
+    const cudaError_t q = cudaEventQuery(R.ev);
+    if (q != cudaErrorNotReady) {
+      R.running = false;
+      R.closing = false;  // a request held back for a larger kernel is published below
+      if (q != cudaSuccess) {
+        R.failed = true;
+        snprintf(sv->err, sizeof(sv->err), "resident serving kernel: %s", cudaGetErrorString(q));
+        cudaGetLastError();
+      }
+      did = true;
+    }
+  }
+  const auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> g(sv->mu);
+  // completions: a done word equal to the request's sequence number + 1
+  // follows its outputs (system-scope fence in the kernel)
+  if (R.n_flight > 0) {
+    for (int c = 0; c < 2; ++c) {
+      for (RingReq& x : R.flight[c]) {
+        if (x.done) continue;
+        const bool ok = *reinterpret_cast<volatile unsigned*>(&R.h_done[x.rq]) == x.seq + 1u;
+        if (!ok && !(R.failed && !R.running)) continue;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        ServerDone d;
+        d.robot = x.r.robot;
+        for (int k = 0; k < 8; ++k) d.out[k] = ok ? R.h_out[8 * (size_t)x.rq + k] : NAN;
+        d.latency = std::chrono::duration<double>(now - x.r.t0).count();
+        d.queue = std::chrono::duration<double>(x.t_publish - x.r.t0).count();
+        d.device = std::chrono::duration<double>(now - x.t_publish).count();
+        d.cls = x.cls;
+        d.status = ok ? MPPI_OK : MPPI_ECUDA;
+        sv->done.push_back(d);
+        sv->busy[x.r.robot] = 0;
+        sv->n_inflight--;
+        sv->requests++;
+        x.done = true;
+        R.free_rq.push_back(x.rq);
+        R.n_flight--;
+        R.flight_ops[c] -= x.ops;
+        if (R.n_flight == 0) R.flight_ops[0] = R.flight_ops[1] = 0.0;  // no drift
+        did = true;
+      }
+      while (!R.flight[c].empty() && R.flight[c].front().done) R.flight[c].pop_front();
+    }
+  }
+  // publication, small class first: each request's inputs and entry, then
+  // its items, then (release) the class's published count
+  bool pub_any[2] = {false, false};
+  for (int c = 0; c < 2 && !R.failed; ++c) {
+    std::deque<ServerReq>& qu = sv->queue[c];
+    // the requests held on the host are published least work first (the
+    // age limit first), up to the class's cap on published, unfinished work
+    const double cap = c == 0 ? sv->pol.batch_ops_small : sv->pol.batch_ops_large;
+    if (sv->pol.shortest_first && qu.size() > 1) {
+      const double lim = sv->pol.max_wait_s;
+      std::stable_sort(qu.begin(), qu.end(), [&](const ServerReq& a, const ServerReq& b2) {
+        const bool oa = lim > 0 && std::chrono::duration<double>(now - a.t0).count() > lim;
+        const bool ob = lim > 0 && std::chrono::duration<double>(now - b2.t0).count() > lim;
+        if (oa != ob) return oa;
+        if (oa) return a.t0 < b2.t0;
+        return a.ops < b2.ops;
+      });
+    }
+    while (!qu.empty() && !R.closing) {
+      ServerReq& r = qu.front();
+      if (cap > 0 && R.flight_ops[c] > 0 && R.flight_ops[c] + r.ops > cap) break;
+      const BatchSlot& s = sv->b->slots[r.robot];
+      const unsigned nt = (unsigned)s.D.nTiles;
+      if (s.smem > R.max_dyn) {  // cannot run in the serving kernel at all
+        ServerDone d;
+        d.robot = r.robot;
+        for (int k = 0; k < 8; ++k) d.out[k] = NAN;
+        d.latency = d.queue = std::chrono::duration<double>(now - r.t0).count();
+        d.device = 0.0;
+        d.cls = c;
+        d.status = MPPI_EINVAL;
+        sv->done.push_back(d);
+        sv->busy[r.robot] = 0;
+        sv->n_inflight--;
+        qu.pop_front();
+        continue;
+      }
+      if (R.running && (s.smem > R.k_smem || (s.p.model >= 2 && !R.k_all))) {
+        // the running kernel was launched for smaller tiles or fewer models:
+        // let it finish what it has claimed, then launch one that fits
+        R.closing = true;
+        *reinterpret_cast<volatile unsigned*>(&R.h_hdr->closed) = 1u;
+        break;
+      }
+      const unsigned wm = R.flight[c].empty() ? R.pub[c] : R.flight[c].front().item_begin;
+      if (R.free_rq.empty() || R.pub[c] + nt - wm > R.cap_items) break;  // rings full
+      const int rq = R.free_rq.back();
+      R.free_rq.pop_back();
+      const int n = s.n, T = s.p.T;
+      double* in = R.h_in + (size_t)rq * R.in_stride;
+      memcpy(in, r.x0, sizeof(double) * n);
+      if (!r.xref.empty()) {
+        memcpy(in + n, r.xref.data(), sizeof(double) * (size_t)(T + 1) * n);
+      } else {
+        for (int t = 0; t <= T; ++t) memcpy(in + n + (size_t)t * n, s.p.x_goal, sizeof(double) * n);
+      }
+      R.h_reqs[rq] = ServeReq{r.robot, n, n * (T + 2), R.seq};
+      WorkItem* items = R.h_items[c];
+      for (unsigned t = 0; t < nt; ++t)
+        items[(R.pub[c] + t) & (R.cap_items - 1u)] = WorkItem{rq, (int)t};
+      RingReq x;
+      x.r = std::move(r);
+      x.rq = rq;
+      x.seq = R.seq++;
+      x.cls = c;
+      x.ops = x.r.ops;
+      x.item_begin = R.pub[c];
+      x.t_publish = now;
+      R.flight_ops[c] += x.ops;
+      R.pub[c] += nt;
+      R.flight[c].push_back(std::move(x));
+      R.n_flight++;
+      qu.pop_front();
+      pub_any[c] = true;
+      did = true;
+    }
+  }
+  if (R.failed) {  // a failed kernel leaves nothing to run the queued requests
+    for (int c = 0; c < 2; ++c) {
+      for (ServerReq& r : sv->queue[c]) {
+        ServerDone d;
+        d.robot = r.robot;
+        for (int k = 0; k < 8; ++k) d.out[k] = NAN;
+        d.latency = d.queue = std::chrono::duration<double>(now - r.t0).count();
+        d.device = 0.0;
+        d.cls = c;
+        d.status = MPPI_ECUDA;
+        sv->done.push_back(d);
+        sv->busy[r.robot] = 0;
+        sv->n_inflight--;
+        did = true;
+      }
+      sv->queue[c].clear();
+    }
+  }
+  if (pub_any[0] || pub_any[1]) {
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    for (int c = 0; c < 2; ++c)
+      if (pub_any[c]) *reinterpret_cast<volatile unsigned*>(&R.h_hdr->published[c]) = R.pub[c];
+  }
+  // close the kernel once it has had nothing to do for a while
+  const bool busy = R.n_flight > 0 || !sv->queue[0].empty() || !sv->queue[1].empty();
+  if (busy) R.last_busy = now;
+  if (R.running && !R.closing && !busy &&
+      std::chrono::duration<double>(now - R.last_busy).count() > kServeIdleClose) {
+    R.closing = true;
+    *reinterpret_cast<volatile unsigned*>(&R.h_hdr->closed) = 1u;
+    did = true;
+  }
+  // launch when work is published and no kernel runs
+  if (!R.running && R.n_flight > 0 && dev_ok && !R.failed) {
+    *reinterpret_cast<volatile unsigned*>(&R.h_hdr->closed) = 0u;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    R.closing = false;
+    const int smem = std::min(std::max(sv->max_slot_smem, 16), R.max_dyn);
+    const bool all = sv->any_all;
+    const auto kernel = all ? serve_kernel_all : serve_kernel;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchThreads, smem) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      R.failed = true;
+      snprintf(sv->err, sizeof(sv->err), "resident serving kernel does not fit (%d bytes)", smem);
+      return true;
+    }
+    // one CTA slot stays free, so a joining robot's set-up kernel can run
+    const int grid = std::max(1, num_sms() * occ - 1);
+    ServeRing ring;
+    ring.hdr = R.d_hdr;
+    ring.items[0] = R.d_items[0];
+    ring.items[1] = R.d_items[1];
+    ring.reqs = R.d_reqs;
+    ring.inputs = R.d_in;
+    ring.out = R.d_out;
+    ring.done = R.d_done;
+    ring.next = R.d_next;
+    ring.cap_items = R.cap_items;
+    ring.in_stride = R.in_stride;
+    ring.idle_polls = kServeIdlePolls;
+    ring.idle_ns = kServeIdleNs;
+    kernel<<<grid, kBatchThreads, smem, R.stream>>>(sv->b->d_descs, ring);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(R.ev, R.stream) != cudaSuccess) {
+      R.failed = true;
+      snprintf(sv->err, sizeof(sv->err), "resident serving kernel launch failed");
+      cudaGetLastError();
+      return true;
+    }
+    R.running = true;
+    R.k_smem = smem;
+    R.k_all = all;
+    sv->batches++;
+    did = true;
+  }
+  return did;
+}
+
 void server_loop(mppi_server* sv) {
   // a new host thread starts on device 0: take the server's device, where
   // its pool, streams and events were made, before any other CUDA call
@@ -2067,6 +2412,10 @@ void server_loop(mppi_server* sv) {
   std::vector<double> x0s;
   std::vector<const double*> xr;
   while (!sv->stop.load()) {
+    if (sv->dq.load()) {
+      if (!ring_step(sv, dev_ok)) std::this_thread::sleep_for(std::chrono::microseconds(10));
+      continue;
+    }
     bool did = false;
     for (size_t i = 0; i < sv->lanes.size(); ++i) {
       if (!sv->lane_busy[i]) continue;
@@ -2215,7 +2564,7 @@ int mppi_server_create(int32_t max_robots, size_t pool_bytes, int32_t lanes, mpp
   sv->lane_busy.assign(lanes, 0);
   sv->joined.assign(max_robots, 0);
   sv->busy.assign(max_robots, 0);
-  sv->pol = mppi_server_policy{0.0, 1, 0, 0.75, 0.0, 0.0, 0.0};  // one class, oldest first
+  sv->pol = mppi_server_policy{0.0, 1, 0, 0.75, 0.0, 0.0, 0.0, 0, 0};  // one class, oldest first
   assign_lanes(sv);
   // staging for a step of every robot at once (step table, inputs, a
   // generous work list), made now so that the scheduler never has to grow it
@@ -2256,11 +2605,17 @@ int mppi_server_set_policy(mppi_server* sv, const mppi_server_policy* pol) {
     return fail(MPPI_EINVAL, "shortest_first must be 0 or 1");
   if (!std::isfinite(pol->max_wait_s) || pol->max_wait_s < 0)
     return fail(MPPI_EINVAL, "max_wait_s must be finite and >= 0");
+  if (pol->device_queue != 0 && pol->device_queue != 1)
+    return fail(MPPI_EINVAL, "device_queue must be 0 or 1");
   std::lock_guard<std::mutex> g(sv->mu);
   if (sv->n_inflight.load() != 0)
     return fail(MPPI_ESTATE, "requests are queued or in flight: set the policy while idle");
+  if (pol->device_queue) {
+    if (int rc = ring_alloc(sv)) return rc;
+  }
   sv->pol = *pol;
   assign_lanes(sv);
+  sv->dq = pol->device_queue != 0;
   return MPPI_OK;
 }
 
@@ -2285,6 +2640,8 @@ int mppi_server_join(mppi_server* sv, const mppi_params* p, const double* u_init
   std::lock_guard<std::mutex> g(sv->mu);
   sv->joined[slot] = 1;
   sv->busy[slot] = 0;
+  sv->max_slot_smem = std::max(sv->max_slot_smem, sv->b->slots[slot].smem);
+  sv->any_all = sv->any_all || p->model >= 2;
   *robot = slot;
   return MPPI_OK;
 }
@@ -2320,7 +2677,7 @@ int mppi_server_submit(mppi_server* sv, int32_t robot, const double* x0, const d
     if (!finite_all(r.xref.data(), (int)r.xref.size())) return fail(MPPI_EINVAL, "xref is not finite");
   }
   r.ops = slot_ops(s);
-  bool two = false;
+  bool two = sv->pol.device_queue != 0 && sv->pol.small_ops_max > 0;
   for (int c : sv->lane_cls) two = two || c == 1;
   r.cls = (two && r.ops > sv->pol.small_ops_max) ? 1 : 0;
   sv->busy[robot] = 1;
@@ -2382,6 +2739,7 @@ int mppi_server_destroy(mppi_server* sv) {
   if (!sv) return MPPI_OK;
   sv->stop = true;
   if (sv->worker.joinable()) sv->worker.join();
+  ring_free(sv->ring);
   for (size_t i = 0; i < sv->lanes.size(); ++i) {
     free_lane(sv->lanes[i]);
     cudaEventDestroy(sv->ev_start[i]);

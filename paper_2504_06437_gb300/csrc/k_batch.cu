@@ -5,8 +5,6 @@
 
 namespace dbm {
 
-__device__ __forceinline__ int npos_code(int npos) { return npos == 14 ? 1 : 0; }
-
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const CtrlDesc* __restrict__ descs,
                                                               unsigned char* stage,
                                                               double* __restrict__ u0_out) {
@@ -46,6 +44,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const CtrlDesc* __
     }
     __syncthreads();  // Ds and s_item are reused by the next item
   }
+}
+
+// Resident serving kernel over the same tile instantiations (see
+// serve_body in kernels.cuh).
+__global__ void __launch_bounds__(kBatchThreads) serve_kernel(const CtrlDesc* __restrict__ descs,
+                                                              ServeRing R) {
+  serve_body<false>(descs, R);
 }
 
 }  // namespace dbm

@@ -8,8 +8,6 @@
 
 namespace dbm {
 
-__device__ __forceinline__ int npos_code(int npos) { return npos == 14 ? 1 : 0; }
-
 // At least two resident CTAs per SM: without the bound the allocation would
 // follow the largest of its eight tile instantiations (249 registers, one
 // CTA per SM).
@@ -55,6 +53,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel_all(
     }
     __syncthreads();  // Ds and s_item are reused by the next item
   }
+}
+
+// Resident serving kernel over the same tile instantiations (see
+// serve_body in kernels.cuh).
+__global__ void __launch_bounds__(kBatchThreads, 2) serve_kernel_all(const CtrlDesc* __restrict__ descs,
+                                                              ServeRing R) {
+  serve_body<true>(descs, R);
 }
 
 }  // namespace dbm

@@ -32,11 +32,17 @@ def wait_all(srv, n, timeout=60.0):
     return got
 
 
-def test_served_results_equal_alone(gpu):
+@pytest.mark.parametrize("mode", ["lanes", "device_queue"])
+def test_served_results_equal_alone(gpu, mode):
+    """Staggered arrivals over three closed-loop rounds; each robot's controls
+    equal the same robot alone, bit for bit.  device_queue: the resident
+    kernel takes requests that arrive while it runs."""
     g = W.rng(11)
     worlds = [W._mixed_world(g, i, 11, 256, 6000, 10, 60, 5, 120) for i in range(7)]
     rounds = 3
     with gpu.Server(16, 512 << 20, lanes=2) as srv:
+        if mode == "device_queue":
+            srv.set_policy(small_ops_max=2e7, device_queue=True)
         robots = [srv.join(w.params, w.obstacles) for w in worlds]
         assert all(r is not None for r in robots)
         x = {r: w.x_start.copy() for r, w in zip(robots, worlds)}
@@ -68,7 +74,7 @@ def test_served_results_equal_alone(gpu):
             assert time.time() - t0 < 60
         st = srv.stats()
         assert st["requests"] == rounds * len(robots)
-        assert st["batches"] < st["requests"]          # requests were batched
+        assert st["batches"] < st["requests"]          # requests shared launches
     for r, w in zip(robots, worlds):
         p = w.params
         S = min(32, p["K"])
@@ -105,10 +111,13 @@ def test_admission_refused_then_granted(gpu):
         assert rid == r and st == 0 and np.all(np.isfinite(u0))
 
 
-def test_many_requests_complete(gpu):
+@pytest.mark.parametrize("mode", ["lanes", "device_queue"])
+def test_many_requests_complete(gpu, mode):
     g = W.rng(5)
     worlds = [W._mixed_world(g, i, 5, 128, 2048, 10, 40, 5, 60) for i in range(40)]
     with gpu.Server(64, 512 << 20, lanes=3) as srv:
+        if mode == "device_queue":
+            srv.set_policy(small_ops_max=0.0, device_queue=True)
         robots = [srv.join(w.params, w.obstacles) for w in worlds]
         for r, w in zip(robots, worlds):
             srv.submit(r, w.x_start)
@@ -120,7 +129,8 @@ def test_many_requests_complete(gpu):
         wait_all(srv, 1)
 
 
-def test_size_classes_small_request_passes_large(gpu):
+@pytest.mark.parametrize("mode", ["lanes", "device_queue"])
+def test_size_classes_small_request_passes_large(gpu, mode):
     """Under a size-class policy a small request submitted just after a large
     one completes first: the large class's kernel leaves part of the GPU to
     the small class's lane, so the small request does not wait for it.  The
@@ -132,10 +142,11 @@ def test_size_classes_small_request_passes_large(gpu):
     small = W.unicycle_small(4)
     with gpu.Server(4, 1 << 30, lanes=2) as srv:
         srv.set_policy(small_ops_max=1e9, small_lanes=1, large_share=0.75, shortest_first=True,
-                       max_wait_s=0.05)
+                       max_wait_s=0.05, device_queue=mode == "device_queue")
         pol = srv.get_policy()
         assert pol["shortest_first"] and pol["max_wait_s"] == 0.05
         assert pol["lane_classes"] == [0, 1]
+        assert pol["device_queue"] == (mode == "device_queue")
         rb = srv.join(big.params, big.obstacles)
         rs = srv.join(small.params, small.obstacles)
         srv.submit(rb, big.x_start)
@@ -176,3 +187,38 @@ def test_policy_rejects_bad_values(gpu):
             with pytest.raises(gpu.MppiError) as e:
                 srv.set_policy(**bad)
             assert e.value.code == gpu.MPPI_EINVAL
+
+
+def test_device_queue_relaunches_for_larger_tiles(gpu):
+    """A robot whose tiles need more shared memory than the running resident
+    kernel was launched with joins while that kernel works (six long
+    requests, about 10 ms of device time, with smaller tiles): the scheduler
+    closes the kernel, launches one that fits, and every request completes
+    with the same controls as the robot alone."""
+    g = W.rng(8)
+    longs = []
+    for i in range(6):
+        w = W.unicycle_stress(20 + i, K=65536, T=60)
+        w.obstacles = W.obstacle_field(g, 1000, (0, 0), (50, 50), 0.1, 1.0, keep_clear=(w.x_start, w.goal))
+        longs.append(w)
+    big = W.quad2d(6, K=8192, T=100)
+    with gpu.Server(8, 1 << 30, lanes=2) as srv:
+        srv.set_policy(small_ops_max=0.0, device_queue=True)
+        robots = [srv.join(w.params, w.obstacles) for w in longs]
+        for r, w in zip(robots, longs):
+            srv.submit(r, w.x_start)
+        time.sleep(0.001)
+        rb = srv.join(big.params, big.obstacles)
+        srv.submit(rb, big.x_start)
+        got = wait_all(srv, len(robots) + 1)
+        assert all(d[4] == 0 for d in got)
+        res = {d[0]: d[1] for d in got}
+        assert srv.stats()["batches"] >= 2   # the kernel was closed and launched again
+    for r, w in list(zip(robots, longs)) + [(rb, big)]:
+        with gpu.Batch(2, 1 << 30) as b:
+            info = b.slot_info(b.add(w.params, w.obstacles))
+        with gpu.Controller(w.params, tiling=dict(samples_per_cta=info["samples_per_cta"], threads=256,
+                                                  positions_per_thread=info["positions_per_thread"])) as c:
+            c.set_obstacles(w.obstacles)
+            c.step(w.x_start)
+            np.testing.assert_array_equal(c.get_control(), res[r])
