@@ -222,3 +222,30 @@ def test_device_queue_relaunches_for_larger_tiles(gpu):
             c.set_obstacles(w.obstacles)
             c.step(w.x_start)
             np.testing.assert_array_equal(c.get_control(), res[r])
+
+
+def test_server_on_second_device(gpu):
+    """A server created while device 1 is current keeps its pool, streams and
+    scheduler thread on device 1 (the scheduler thread starts on device 0
+    unless it takes the server's device).  Needs two visible GPUs."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    w = W.unicycle_small(12)
+    prev = torch.cuda.current_device()
+    try:
+        torch.cuda.set_device(1)
+        with gpu.Server(4, 64 << 20, lanes=2) as srv:
+            r = srv.join(w.params, w.obstacles)
+            srv.submit(r, w.x_start)
+            (rid, u0, x1, lat, st), = wait_all(srv, 1)
+            assert rid == r and st == 0
+        with gpu.Batch(2, 64 << 20) as b:
+            info = b.slot_info(b.add(w.params, w.obstacles))
+        with gpu.Controller(w.params, tiling=dict(samples_per_cta=info["samples_per_cta"], threads=256,
+                                                  positions_per_thread=info["positions_per_thread"])) as c:
+            c.set_obstacles(w.obstacles)
+            c.step(w.x_start)
+            np.testing.assert_array_equal(c.get_control(), u0)
+    finally:
+        torch.cuda.set_device(prev)
