@@ -423,6 +423,7 @@ struct TileScratch {
   float ref;                           // common reference of a merge (minimum of the sources' rho)
   double S_e_used, S_e_next;           // exploration rate of this step and the next
   unsigned long long iter;             // iteration counter of this step
+  double x0[2];                        // measured position: origin of the tile's frame
 };
 
 // The grid map as a tile reads it.  The tile's frame is centred on the
@@ -645,9 +646,15 @@ __device__ __forceinline__ float key_min(unsigned k) {
 
 // Merge n partial results (rho_i, Z_i, cols_i[ncol]), each taken relative to
 // its own minimum rho_i, into one relative to ref = min_i rho_i.hi: the
-// log-sum-exp merge of Eq. 4's numerator and denominator.  Source i is scaled
-// by s_i = exp(-(rho_i - ref) / lambda) <= 1 (thread i computes it while the
-// column loads are in flight).  The ncol columns are read as ncp = ncol / 2
+// log-sum-exp merge of Eq. 4's numerator and denominator.  ref is read from
+// *minw, the key (min_key) into which every source put its rho_i.hi with an
+// atomic maximum before its ticket; thread 0 clears the word for the next
+// step once every thread has read it, and stores ref at *ref_out.  Source i
+// is scaled by s_i = exp(-(rho_i - ref) / lambda) <= 1.  Every load of the
+// merge (the word, a thread's first source row, its column pairs) is issued
+// before the first of them is used: one memory round trip, which is most of
+// what a merge costs when one CTA runs it alone at the end of a step.  The
+// ncol columns are read as ncp = ncol / 2
 // float pairs: thread tid takes the cell (row group rg, column pair cp) =
 // (tid / ncp, tid % ncp), i.e. rows rg, rg + RG, ... of that pair, up to
 // kMergeLoads rows in flight; the threads with cp = 0 also add s_i Z_i.  The
@@ -662,9 +669,9 @@ __device__ __forceinline__ float key_min(unsigned k) {
 // Outputs in shared memory: *Z_out, col_hi/col_lo[ncol].
 template <bool PIPELINED>
 __device__ inline void merge_partials(int n, const float4* rz, const float* cols, int ncol,
-                                      float ref, float inv_lambda, float* scl, float2* zi, FF* buf,
-                                      FF* Z_out, float* col_hi, float* col_lo, int tid,
-                                      int nthreads) {
+                                      unsigned* minw, float inv_lambda, float* scl, float2* zi,
+                                      FF* buf, float* ref_out, FF* Z_out, float* col_hi,
+                                      float* col_lo, int tid, int nthreads) {
   const int ncp = ncol >> 1;
   const int RG = merge_row_groups(ncol, nthreads);
   const int ncell = RG * ncp;
@@ -695,14 +702,25 @@ __device__ inline void merge_partials(int n, const float4* rz, const float* cols
       }
     }
   };
-  load(va, tid, 0);  // issued before the scales are known
+  const unsigned kmin = __ldcg(minw);
+  const float4 c0 = tid < n ? __ldcg(rz + tid) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  load(va, tid, 0);
   if constexpr (PIPELINED) load(vb, tid, KB);
-  for (int i = tid; i < n; i += nthreads) {
+  const float ref = key_min(kmin);
+  if (tid < n) {
+    scl[tid] = expf(-((c0.x - ref) + c0.y) * inv_lambda);
+    zi[tid] = make_float2(c0.z, c0.w);
+  }
+  for (int i = tid + nthreads; i < n; i += nthreads) {  // more sources than threads
     const float4 c = __ldcg(rz + i);
     scl[i] = expf(-((c.x - ref) + c.y) * inv_lambda);
     zi[i] = make_float2(c.z, c.w);
   }
   __syncthreads();
+  if (tid == 0) {
+    *ref_out = ref;
+    *minw = 0u;
+  }
   for (int cell = tid; cell < ncell; cell += nthreads) {
     const int rg = cell / ncp, cp = cell - rg * ncp;
     FF a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, z = {0.0f, 0.0f};

@@ -382,9 +382,17 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
 // kept), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"), S_e
 // (Eq. 10, C_B floored at 0 inside the logarithm) and the state update.  The
 // next step's constants that do not depend on S_e (u_t in FP32, a'_t = gamma
-// Sigma^-1 u_t and sum_t u_t . a'_t) are formed in the same pass as U* and
-// the shift, one step per thread; S_e enters afterwards through L, C0 and
-// the 1 / S_e that the next step applies to a'_t.
+// Sigma^-1 u_t and sum_t u_t . a'_t) are formed with the shift, one step per
+// thread; S_e enters afterwards through L, C0 and the 1 / S_e that the next
+// step applies to a'_t.
+// One CTA runs this alone at the end of the step, so its length is a chain
+// of latencies: the measured position comes from the tile's scratch (no
+// memory round trip), and the lanes of a warp meet (__syncwarp) before the
+// shuffles of a reduction that follows a loop they left at different
+// steps.  Each thread forms u*_t and u*_{t+1} itself, which is faster here
+// than forming each entry once and reading the neighbour after a barrier
+// (that costs another barrier and more code, which a step run after an L2
+// flush fetches from memory).
 // The grid map in the tile's frame, whose origin is the measured position
 // (x0g[0], x0g[1]).  FP64, so one thread builds it (grid_shared) and the
 // others read it from shared memory.
@@ -440,8 +448,7 @@ __device__ __forceinline__ void sgf_columns(const float* __restrict__ w, int W, 
 
 template <int MODEL, int NPOS, bool GRID = false>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
-                            const double* __restrict__ x0g, double* out,
-                            const GridView* gv = nullptr) {
+                            double* out, const GridView* gv = nullptr) {
   const int tid = threadIdx.x, nthreads = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int T = D.T, P = D.P;
   const double* Us = reinterpret_cast<const double*>(smem + L.Us);  // the step's U
@@ -485,6 +492,7 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
     ff_add_prod(c0, v0, a0, 0.0f);
     ff_add_prod(c0, v1, a1, 0.0f);
   }
+  __syncwarp();
   c0 = warp_sum_ff(c0);
   if (lane == 0) {
     redf[2 * warp] = c0.hi;
@@ -507,6 +515,7 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       for (int p = 0; p < P; ++p) b += fabsf(b_nom[t * P + p]);
       ff_add_prod(a, cw[t], b, 0.0f);
     }
+    __syncwarp();
     a = warp_sum_ff(a);
     FF cs = lane < (nthreads >> 5) ? FF{redf[2 * lane], redf[2 * lane + 1]} : FF{0.0f, 0.0f};
     cs = warp_sum_ff(cs);
@@ -538,8 +547,8 @@ __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, 
       }
       constexpr int n = Dyn<MODEL>::n;
       double xn[6] = {0, 0, 0, 0, 0, 0};
-      xn[0] = x0g[0] + (double)x1[0];  // back from the frame centred on x0
-      xn[1] = x0g[1] + (double)x1[1];
+      xn[0] = ts.x0[0] + (double)x1[0];  // back from the frame centred on x0
+      xn[1] = ts.x0[1] + (double)x1[1];
       for (int d = 2; d < n; ++d) xn[d] = (double)x1[d];
       for (int d = 0; d < 6; ++d) st->x1[d] = xn[d];
       if (out) {  // batched launches: u0 then the predicted state, 8 doubles
@@ -654,6 +663,8 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
   if (tid == 0) {  // read early: only the final stage uses them
     ts.S_e_used = S_e;
     ts.iter = iter;
+    ts.x0[0] = ox;
+    ts.x0[1] = oy;
     if constexpr (GRID) grid_shared() = grid_view(D, x0g);  // read after the next barrier
   }
   if (J > 0) {
@@ -840,9 +851,9 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
 
   // ---- two-level last-arriver merge.  The CTA's writes are published by
   // one thread: barrier, fence, ticket; the last arriver fences again before
-  // the barrier that releases its threads to read the others' partials.  It
-  // takes (and clears) the group's minimum word, the exact minimum of its
-  // members' rho.
+  // the barrier that releases its threads to read the others' partials.  The
+  // merge reads (and clears) the group's minimum word, the exact minimum of
+  // its members' rho.
   __syncthreads();
   const int g = tile / D.GT;
   const int m0 = g * D.GT;
@@ -854,7 +865,6 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
     ts.flag = (tk == (unsigned)(members - 1));
     if (ts.flag) {
       __threadfence();
-      ts.ref = key_min(atomicExch(&minw[g], 0u));
       D.counters[g] = 0u;
     }
   }
@@ -866,8 +876,9 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
   const int ncol = 2 * T;
   FF* mbuf = reinterpret_cast<FF*>(smem + L.region);
   float2* zi = reinterpret_cast<float2*>(smem + L.region + merge_buf_bytes(ncol, nthreads));
-  merge_partials<!BATCHED>(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, ts.ref,
-                 D.inv_lambda_f, scl, zi, mbuf, &ts.Z, col_hi, col_lo, tid, nthreads);
+  merge_partials<!BATCHED>(members, D.part_rz + m0, D.part + (size_t)m0 * ncol, ncol, &minw[g],
+                           D.inv_lambda_f, scl, zi, mbuf, &ts.ref, &ts.Z, col_hi, col_lo, tid,
+                           nthreads);
   if (D.nGroups > 1) {
     for (int c = tid; c < ncol; c += nthreads) D.gpart[(size_t)g * ncol + c] = col_hi[c] + col_lo[c];
     if (tid == 0) {
@@ -881,14 +892,14 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
       ts.flag = (tk == (unsigned)(D.nGroups - 1));
       if (ts.flag) {
         __threadfence();
-        ts.ref = key_min(atomicExch(&minw[D.nGroups], 0u));
         D.counters[D.nGroups] = 0u;
       }
     }
     __syncthreads();
     if (!ts.flag) return;
-    merge_partials<!BATCHED>(D.nGroups, D.gpart_rz, D.gpart, ncol, ts.ref, D.inv_lambda_f, scl, zi, mbuf,
-                   &ts.Z, col_hi, col_lo, tid, nthreads);
+    merge_partials<!BATCHED>(D.nGroups, D.gpart_rz, D.gpart, ncol, &minw[D.nGroups],
+                             D.inv_lambda_f, scl, zi, mbuf, &ts.ref, &ts.Z, col_hi, col_lo, tid,
+                             nthreads);
   }
   if constexpr (SGF) {
     if (D.sgf_wp)
@@ -898,9 +909,9 @@ __device__ __forceinline__ void run_tile_inl(const CtrlDesc& D, int tile,
   if (tid == 0) ts.rho = FF{ts.ref, 0.0f};
   if constexpr (GRID) {
     const GridView gv = grid_shared();
-    final_stage<MODEL, NPOS, true>(D, smem, L, ts, x0g, u0_out, &gv);
+    final_stage<MODEL, NPOS, true>(D, smem, L, ts, u0_out, &gv);
   } else {
-    final_stage<MODEL, NPOS>(D, smem, L, ts, x0g, u0_out);
+    final_stage<MODEL, NPOS>(D, smem, L, ts, u0_out);
   }
 }
 
