@@ -781,6 +781,9 @@ def main():
 
     # end to end through the host API (pinned staging inside the library)
     u0 = ctl.get_control()
+    for _ in range(max(3, args.warmup)):  # untimed: the host path's own warm-up
+        ctl.step(x0, xref, stream)
+        u0 = ctl.get_control()
     e2e_t = []
     for i in range(args.e2e_steps):
         flush.fill_(float(i & 7))
