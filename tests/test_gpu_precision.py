@@ -83,6 +83,39 @@ def test_precision_against_oracle(gpu, orc, name):
         u0, _ = g.get_control(want_U=True)
         dbg = g.get_debug()
         regs = g.kernel_regs()
+    rec = _compare(name, w, ro, ctl, u0, dbg, tiling, regs)
+    if name in COLLIDING:
+        assert rec["collided"] >= COLLIDING[name][2], rec["collided"]
+
+
+def test_precision_largest_K(gpu, orc):
+    """K at its limit (2^22 samples; T 8, the stress world's eight first
+    circles), in the library's default launch shape: the tiles form 64
+    groups of thousands of rows each, more than the merging CTA has
+    threads, so each thread of a group merge scales several source rows.
+    Every sample compared, as above."""
+    w = W.unicycle_stress(0, K=1 << 22, T=8)
+    w.obstacles = w.obstacles[:8]
+    p = w.params
+    ctl = orc.new_controller(p)
+    x = w.x_start
+    xref = w.reference(x)
+    ro = orc.step(p, w.obstacles, x, xref, ctl)
+    with gpu.Controller(p) as g:
+        g.set_obstacles(w.obstacles)
+        g.step(x, xref)
+        u0, _ = g.get_control(want_U=True)
+        dbg = g.get_debug()
+        regs = g.kernel_regs()
+        tiling = g.tiling()
+    n_tiles = tiling["n_ctas"]
+    assert -(-n_tiles // 64) > tiling["threads"], tiling  # group rows > threads
+    _compare("unicycle_largest_K", w, ro, ctl, u0, dbg, tiling, regs)
+
+
+def _compare(name, w, ro, ctl, u0, dbg, tiling, regs):
+    """Checks one GPU step against the oracle's and prints its PRECISION line."""
+    p = w.params
     rel = np.abs(dbg["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
     u_err = float(np.abs(dbg["Ustar"] - ro["Ustar"]).max())
     w_err, w_self, w_ratio = weight_errors(ro, dbg, float(p["lambda"]))
@@ -104,5 +137,4 @@ def test_precision_against_oracle(gpu, orc, name):
     assert w_self <= SELF_RTOL
     assert w_ratio <= 1.0
     assert mismatch == 0
-    if name in COLLIDING:
-        assert rec["collided"] >= COLLIDING[name][2], rec["collided"]
+    return rec
