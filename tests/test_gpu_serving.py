@@ -179,6 +179,48 @@ def test_size_classes_small_request_passes_large(gpu, mode):
             np.testing.assert_array_equal(c.get_control(), res[r])
 
 
+@pytest.mark.parametrize("mode", ["lanes", "device_queue"])
+def test_leave_refused_in_flight_and_destroy_with_requests_pending(gpu, mode):
+    """A robot cannot leave while its request is queued or running (its slot
+    holds the state the request updates); once the request completes it can,
+    and a robot that left cannot submit.  Destroying the server with
+    requests still queued and running returns: the scheduler stops, the
+    resident kernel finishes what it claimed and the published rest, and the
+    pool is freed."""
+    g = W.rng(21)
+    # four planar quadrotors of about 2e10 operations each (about 1 ms of
+    # the whole GPU): the last one submitted is still pending when its
+    # robot tries to leave
+    worlds = [W.quad2d(21 + i, K=16384, T=80) for i in range(4)]
+    for w in worlds:
+        w.obstacles = W.obstacle_field(g, 300, (0, 0), (20, 10), 0.2, 0.6,
+                                       keep_clear=(w.x_start, w.goal))
+    srv = gpu.Server(8, 1 << 30, lanes=1)
+    try:
+        if mode == "device_queue":
+            srv.set_policy(small_ops_max=0.0, device_queue=True)
+        robots = [srv.join(w.params, w.obstacles) for w in worlds]
+        assert all(r is not None for r in robots)
+        for r, w in zip(robots, worlds):
+            srv.submit(r, w.x_start)
+        with pytest.raises(gpu.MppiError) as e:
+            srv.leave(robots[-1])
+        assert e.value.code == gpu.MPPI_ESTATE
+        got = wait_all(srv, len(robots))
+        assert sorted(x[0] for x in got) == sorted(robots)
+        assert all(x[4] == 0 for x in got)
+        srv.leave(robots[-1])
+        with pytest.raises(gpu.MppiError) as e:
+            srv.submit(robots[-1], worlds[-1].x_start)
+        assert e.value.code == gpu.MPPI_EINVAL
+        for r, w in zip(robots[:-1], worlds[:-1]):
+            srv.submit(r, w.x_start)
+    finally:
+        t0 = time.time()
+        srv.close()            # with up to three requests pending
+        assert time.time() - t0 < 30.0
+
+
 def test_policy_rejects_bad_values(gpu):
     with gpu.Server(4, 64 << 20, lanes=2) as srv:
         for bad in (dict(small_ops_max=-1.0), dict(small_ops_max=1e9, large_share=0.0),
