@@ -182,11 +182,11 @@ def test_size_classes_small_request_passes_large(gpu, mode):
 @pytest.mark.parametrize("mode", ["lanes", "device_queue"])
 def test_leave_refused_in_flight_and_destroy_with_requests_pending(gpu, mode):
     """A robot cannot leave while its request is queued or running (its slot
-    holds the state the request updates); once the request completes it can,
-    and a robot that left cannot submit.  Destroying the server with
-    requests still queued and running returns: the scheduler stops, the
-    resident kernel finishes what it claimed and the published rest, and the
-    pool is freed."""
+    holds the state the request updates), nor can the policy change; once
+    the request completes the robot can leave, and a robot that left cannot
+    submit.  Destroying the server with requests still queued and running
+    returns: the scheduler stops, the resident kernel finishes what it
+    claimed and the published rest, and the pool is freed."""
     g = W.rng(21)
     # four planar quadrotors of about 2e10 operations each (about 1 ms of
     # the whole GPU): the last one submitted is still pending when its
@@ -205,6 +205,9 @@ def test_leave_refused_in_flight_and_destroy_with_requests_pending(gpu, mode):
             srv.submit(r, w.x_start)
         with pytest.raises(gpu.MppiError) as e:
             srv.leave(robots[-1])
+        assert e.value.code == gpu.MPPI_ESTATE
+        with pytest.raises(gpu.MppiError) as e:  # the policy changes only while idle
+            srv.set_policy(small_ops_max=1e9, device_queue=(mode == "device_queue"))
         assert e.value.code == gpu.MPPI_ESTATE
         got = wait_all(srv, len(robots))
         assert sorted(x[0] for x in got) == sorted(robots)
