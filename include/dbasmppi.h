@@ -87,8 +87,8 @@ extern "C" {
  * also for MPPI_QUAD5); wheelbase is L of Eq. 14 (MPPI_ACKERMANN, > 0, whose
  * steering limits must lie inside (-pi/2, pi/2)).
  * sgf_window, sgf_order: Savitzky-Golay smoothing of the weighted
- * perturbation before it is added (Algorithm 1, U* = U + SGF(...); the paper
- * gives no window or order).  0 leaves the update unsmoothed.  Otherwise
+ * perturbation before it is added to U (Algorithm 1 smooths the update this
+ * way; the paper gives no window or order).  0 leaves the update unsmoothed.  Otherwise
  * each control channel of the T x 2 update is replaced, at every t, by the
  * value at t of the degree-sgf_order least-squares polynomial through the
  * sgf_window steps centred on t, or through the first or last sgf_window
@@ -189,8 +189,8 @@ int mppi_step_device(mppi_ctx* c, const double* d_x0, const double* d_xref,
 
 /* After a step: u0 = u*_0 (2 doubles), the control Algorithm 1 actuates on
  * the plant after the update (first element of U* of Eq. 4), and, if U is
- * not NULL, the shifted nominal sequence for the next step (T x 2; the
- * shift of Algorithm 1's last loop, the last element repeated).
+ * not NULL, the shifted nominal sequence for the next step (T x 2;
+ * Algorithm 1's receding-horizon shift, the last element repeated).
  * After mppi_step, u0 and the status word are written by the step itself
  * into mapped pinned host memory, followed (after a system-scope fence) by
  * the step's iteration number.  With U NULL the call then returns as soon

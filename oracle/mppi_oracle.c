@@ -527,7 +527,7 @@ int orc_step(const orc_params* p, const double* obst, int32_t J,
     Minv[2] = -c / det; Minv[3] = a / det;
   }
 
-  /* Sampled rollouts (Algorithm 1, loop over k). */
+  /* Sampled rollouts (Algorithm 1: one rollout per sample k). */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(orc_get_threads())
 #endif
@@ -560,7 +560,7 @@ int orc_step(const orc_params* p, const double* obst, int32_t J,
     for (int d = 0; d < 2; ++d)
       Us[2 * t + d] = clampd(st->U[2 * t + d] + Us[2 * t + d], p->u_min[d], p->u_max[d]);
 
-  /* Nominal rollout of U* (Algorithm 1, "for t = 1..T") for C_B(X*). */
+  /* Nominal rollout of U* over the horizon (Algorithm 1) for C_B(X*). */
   double x[ORC_MAXN], xn[ORC_MAXN];
   memcpy(x, x0, sizeof(double) * n);
   double wn = beta;
@@ -596,7 +596,7 @@ int orc_step(const orc_params* p, const double* obst, int32_t J,
     out->Z = Z;
   }
 
-  /* Shift (Algorithm 1, last loop): u_{t-1} <- u*_t, last element kept. */
+  /* Receding-horizon shift (Algorithm 1): u_{t-1} <- u*_t, last element kept. */
   for (int t = 0; t + 1 < T; ++t) {
     st->U[2 * t] = Us[2 * (t + 1)];
     st->U[2 * t + 1] = Us[2 * (t + 1) + 1];

@@ -654,11 +654,11 @@ __device__ __forceinline__ float key_min(unsigned k) {
 // merge (the word, a thread's first source row, its column pairs) is issued
 // before the first of them is used: one memory round trip, which is most of
 // what a merge costs when one CTA runs it alone at the end of a step.  The
-// ncol columns are read as ncp = ncol / 2
-// float pairs: thread tid takes the cell (row group rg, column pair cp) =
-// (tid / ncp, tid % ncp), i.e. rows rg, rg + RG, ... of that pair, up to
-// kMergeLoads rows in flight; the threads with cp = 0 also add s_i Z_i.  The
-// row groups are then added in order.  All threads of the CTA call it.
+// ncol columns are read as ncp = ncol / 2 float pairs: thread tid takes the
+// cell (row group rg, column pair cp) = (tid / ncp, tid % ncp), i.e. rows
+// rg, rg + RG, ... of that pair, up to kMergeLoads rows in flight; the
+// threads with cp = 0 also add s_i Z_i.  The row groups are then added in
+// order.  All threads of the CTA call it.
 // PIPELINED: the rows in flight are two batches of kMergeLoads / 2, the next
 // loading while one is added; otherwise one batch of kMergeLoads, added
 // before the next is loaded.  Both add the rows in the same order (the same

@@ -377,22 +377,6 @@ __device__ void scan_trajectory(const CtrlDesc& D, int T, const float2* V, int v
   }
 }
 
-// Final stage (one CTA per controller per step): U* from the merged sums
-// (Eq. 4), the shift (Algorithm 1, last loop: u_t <- u*_{t+1}, the last entry
-// kept), nominal rollout of U* for C_B (Algorithm 1, "for t = 1..T"), S_e
-// (Eq. 10, C_B floored at 0 inside the logarithm) and the state update.  The
-// next step's constants that do not depend on S_e (u_t in FP32, a'_t = gamma
-// Sigma^-1 u_t and sum_t u_t . a'_t) are formed with the shift, one step per
-// thread; S_e enters afterwards through L, C0 and the 1 / S_e that the next
-// step applies to a'_t.
-// One CTA runs this alone at the end of the step, so its length is a chain
-// of latencies: the measured position comes from the tile's scratch (no
-// memory round trip), and the lanes of a warp meet (__syncwarp) before the
-// shuffles of a reduction that follows a loop they left at different
-// steps.  Each thread forms u*_t and u*_{t+1} itself, which is faster here
-// than forming each entry once and reading the neighbour after a barrier
-// (that costs another barrier and more code, which a step run after an L2
-// flush fetches from memory).
 // The grid map in the tile's frame, whose origin is the measured position
 // (x0g[0], x0g[1]).  FP64, so one thread builds it (grid_shared) and the
 // others read it from shared memory.
@@ -446,6 +430,22 @@ __device__ __forceinline__ void sgf_columns(const float* __restrict__ w, int W, 
   __syncthreads();
 }
 
+// Final stage (one CTA per controller per step): U* from the merged sums
+// (Eq. 4), Algorithm 1's receding-horizon shift (u_t <- u*_{t+1}, the last
+// entry kept), the nominal rollout of U* over the horizon for C_B, S_e
+// (Eq. 10, C_B floored at 0 inside the logarithm) and the state update.  The
+// next step's constants that do not depend on S_e (u_t in FP32, a'_t = gamma
+// Sigma^-1 u_t and sum_t u_t . a'_t) are formed with the shift, one step per
+// thread; S_e enters afterwards through L, C0 and the 1 / S_e that the next
+// step applies to a'_t.
+// One CTA runs this alone at the end of the step, so its length is a chain
+// of latencies: the measured position comes from the tile's scratch (no
+// memory round trip), and the lanes of a warp meet (__syncwarp) before the
+// shuffles of a reduction that follows a loop they left at different
+// steps.  Each thread forms u*_t and u*_{t+1} itself, which is faster here
+// than forming each entry once and reading the neighbour after a barrier
+// (that costs another barrier and more code, which a step run after an L2
+// flush fetches from memory).
 template <int MODEL, int NPOS, bool GRID = false>
 __device__ void final_stage(const CtrlDesc& D, char* smem, const SmemLayout& L, TileScratch& ts,
                             double* out, const GridView* gv = nullptr) {
