@@ -83,6 +83,7 @@ class _Out(C.Structure):
         ("u0", C.POINTER(C.c_double)),
         ("CB_star", C.c_double), ("beta_used", C.c_double),
         ("beta_d", C.c_double), ("rho", C.c_double), ("Z", C.c_double),
+        ("sens", C.POINTER(C.c_double)), ("reach", C.POINTER(C.c_double)),
     ]
 
 
@@ -113,7 +114,7 @@ def _load():
         lib.orc_step.restype = C.c_int
         lib.orc_sample_costs.argtypes = [C.POINTER(_Params), dp, C.c_int32, dp, dp,
                                          C.POINTER(_State), C.POINTER(C.c_int32), C.c_int32,
-                                         dp, C.POINTER(C.c_uint8), dp]
+                                         dp, C.POINTER(C.c_uint8), dp, dp, dp]
         lib.orc_sample_costs.restype = C.c_int
         lib.orc_grid_h.argtypes = [C.POINTER(_Params), C.c_double, C.c_double]
         lib.orc_grid_h.restype = C.c_double
@@ -312,8 +313,11 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
     """One Algorithm 1 iteration; mutates ``ctl`` (shift, S_e, beta, iter).
 
     ``xref`` is (T+1) x n.  Returns costs, coll, minh, weights, Ustar, u0,
-    CB_star, beta_used, beta_d, rho, Z, the post-step state, and du_eff
-    (K x T x 2) when ``want_du``."""
+    CB_star, beta_used, beta_d, rho, Z, the post-step state, du_eff
+    (K x T x 2) when ``want_du``, and per sample ``sens`` (the barrier
+    cost's first-order change per unit of position error at every shape
+    point) and ``reach`` (the rollout's largest distance from x0), with
+    which the tests bound the cost error an FP32 rollout may make."""
     lib = _load()
     p = make_params(cfg)
     K, T, n = p.K, p.T, state_dim(p.model)
@@ -327,13 +331,15 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
         "costs": np.zeros(K), "coll": np.zeros(K, dtype=np.uint8),
         "minh": np.zeros(K), "weights": np.zeros(K),
         "Ustar": np.zeros((T, 2)), "u0": np.zeros(2),
+        "sens": np.zeros(K), "reach": np.zeros(K),
     }
     du = np.zeros((K, T, 2)) if want_du else None
     out = _Out(costs=_dp(res["costs"]),
                coll=res["coll"].ctypes.data_as(C.POINTER(C.c_uint8)),
                minh=_dp(res["minh"]), weights=_dp(res["weights"]),
                du_eff=_dp(du) if want_du else C.POINTER(C.c_double)(),
-               Ustar=_dp(res["Ustar"]), u0=_dp(res["u0"]))
+               Ustar=_dp(res["Ustar"]), u0=_dp(res["u0"]),
+               sens=_dp(res["sens"]), reach=_dp(res["reach"]))
     rc = lib.orc_step(C.byref(p), _dp(ob), ob.shape[0], _dp(x0), _dp(xref),
                       C.byref(st), C.byref(out))
     if rc == -2:
@@ -356,8 +362,9 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
 
 
 def sample_costs(cfg: dict, obstacles, x0, xref, ctl: Controller, ks) -> dict:
-    """Cost-to-go, collision flag and min h of the listed samples, from the
-    state ``ctl`` (not modified)."""
+    """Cost-to-go, collision flag, min h, barrier sensitivity and reach (as
+    in ``step``) of the listed samples, from the state ``ctl`` (not
+    modified)."""
     lib = _load()
     p = make_params(cfg)
     T, n = p.T, state_dim(p.model)
@@ -370,7 +377,10 @@ def sample_costs(cfg: dict, obstacles, x0, xref, ctl: Controller, ks) -> dict:
     S = np.zeros(ks.size)
     coll = np.zeros(ks.size, dtype=np.uint8)
     mh = np.zeros(ks.size)
+    sens = np.zeros(ks.size)
+    reach = np.zeros(ks.size)
     lib.orc_sample_costs(C.byref(p), _dp(ob), ob.shape[0], _dp(x0), _dp(xref), C.byref(st),
                          ks.ctypes.data_as(C.POINTER(C.c_int32)), ks.size, _dp(S),
-                         coll.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(mh))
-    return dict(costs=S, coll=coll, minh=mh)
+                         coll.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(mh), _dp(sens),
+                         _dp(reach))
+    return dict(costs=S, coll=coll, minh=mh, sens=sens, reach=reach)

@@ -26,6 +26,11 @@
  *   Alg. 1  SGF: Savitzky-Golay smoothing of the weighted perturbation
  *           (Sec. III-A, last paragraph)                -> orc_sgf, orc_step
  *
+ * Test-only outputs, not part of the method: per sample, the barrier cost's
+ * sensitivity to position error (bsum_grad, summed with Eq. 7's weights in
+ * rollout_sample) and the rollout's reach from x0, with which the tests
+ * bound the cost error an FP32 rollout may make near an obstacle.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11), counter (k, t, iter_lo,
  * iter_hi), key (seed_lo, seed_hi).  The paper does not name a generator.
@@ -275,6 +280,36 @@ void orc_bsum(const orc_params* p, const double* obst, int32_t J,
   if (minh) *minh = mh;
 }
 
+/* Sensitivity of the fused barrier at state x to the positions of its shape
+ * points: the sum over points and obstacles of |dB/dp| = 2 |p - c| / h^2
+ * where h > h_eps (a floored term does not move), and 1 / h^2 for the grid
+ * map's term (a signed-distance map: |grad h| taken as 1).  It is the
+ * first-order change of the barrier sum when every point moves by one unit
+ * of length; the tests scale it by the position error an FP32 rollout may
+ * make, to bound the per-sample cost error of samples that pass close to
+ * an obstacle (test infrastructure, not part of the method). */
+static double bsum_grad(const orc_params* p, const double* obst, int32_t J, const double* x) {
+  double c = cos(x[2]), s = sin(x[2]);
+  double G = 0.0;
+  for (int i = 0; i < p->n_shape; ++i) {
+    double sx = p->shape[2 * i], sy = p->shape[2 * i + 1];
+    double px = x[0] + c * sx - s * sy;
+    double py = x[1] + s * sx + c * sy;
+    for (int j = 0; j < J; ++j) {
+      double dx = px - obst[3 * j];
+      double dy = py - obst[3 * j + 1];
+      double r = obst[3 * j + 2];
+      double h = dx * dx + dy * dy - r * r;
+      if (h > p->h_eps) G += 2.0 * sqrt(dx * dx + dy * dy) / (h * h);
+    }
+    if (p->grid) {
+      const double h = orc_grid_h(p, px, py);
+      if (h > p->h_eps) G += 1.0 / (h * h);
+    }
+  }
+  return G;
+}
+
 /* Roll the plant forward under a given control sequence V (T x 2), no
  * noise, no clamping: X is (T+1) x n. */
 void orc_simulate(const orc_params* p, const double* x0, const double* V,
@@ -308,21 +343,24 @@ static double nsum_get(const nsum* a) { return a->s + a->c; }
  *    (Algorithm 1 accumulates after each step).
  *  - control cost gamma u_t^T (S_e Sigma)^-1 v_t (Algorithm 1 form).
  *  - collided step adds C_coll; collision means min h <= 0.
- * Minv = (S_e Sigma)^-1 (row-major), ignored when gamma_ctrl == 0. */
+ * Minv = (S_e Sigma)^-1 (row-major), ignored when gamma_ctrl == 0.
+ * Optional test outputs: *sens_out = sum_t (dS/dB_t) bsum_grad(x_{t+1}),
+ * where the Eq. 7 recursion gives dS/dB_t = R_B sum_{t' >= t} gamma^(t'-t),
+ * and *reach_out = max_t |(x, y)_{t+1} - (x, y)_0|. */
 static void rollout_sample(const orc_params* p, const double* obst, int32_t J,
                            const double* x0, const double* xref,
                            const double* U, double S_e, double beta0,
                            double beta_d, uint64_t iter, int32_t k,
                            const double Minv[4], double* S_out,
                            uint8_t* coll_out, double* minh_out,
-                           double* du_eff) {
+                           double* du_eff, double* sens_out, double* reach_out) {
   const int n = state_dim(p->model);
   double x[ORC_MAXN], xn[ORC_MAXN];
   memcpy(x, x0, sizeof(double) * n);
   double w = beta0;
   nsum S = {0.0, 0.0};
   int coll = 0;
-  double minh = INFINITY;
+  double minh = INFINITY, sens = 0.0, reach = 0.0;
   for (int t = 0; t < p->T; ++t) {
     double du[2], v[2];
     orc_noise(p, S_e, k, t, iter, du, NULL);
@@ -353,6 +391,13 @@ static void rollout_sample(const orc_params* p, const double* obst, int32_t J,
     if (c) nsum_add(&S, p->C_coll);
     coll |= c;
     if (mh < minh) minh = mh;
+    if (sens_out) {
+      const double g = p->gamma_bas, m = (double)(p->T - t);
+      const double dS_dB = p->R_B * (fabs(1.0 - g) > 1e-12 ? (1.0 - pow(g, m)) / (1.0 - g) : m);
+      sens += dS_dB * bsum_grad(p, obst, J, x);
+    }
+    const double dist = hypot(x[0] - x0[0], x[1] - x0[1]);
+    if (dist > reach) reach = dist;
   }
   double phi = 0.0;
   for (int d = 0; d < n; ++d) {
@@ -363,6 +408,8 @@ static void rollout_sample(const orc_params* p, const double* obst, int32_t J,
   *S_out = nsum_get(&S);
   *coll_out = (uint8_t)coll;
   *minh_out = minh;
+  if (sens_out) *sens_out = sens;
+  if (reach_out) *reach_out = reach;
 }
 
 /* Eq. 4 weights: rho = min_k S_k, e_k = exp(-(S_k - rho) / lambda),
@@ -474,6 +521,8 @@ typedef struct {
   double beta_used; /* barrier state the rollouts started from */
   double beta_d;    /* B summed at the goal pose */
   double rho, Z;
+  double* sens;     /* K: barrier sensitivity to position (rollout_sample), or NULL */
+  double* reach;    /* K: farthest distance of the rollout from x0, or NULL */
 } orc_out;
 
 static int g_threads = 0;
@@ -534,7 +583,8 @@ int orc_step(const orc_params* p, const double* obst, int32_t J,
   for (int k = 0; k < K; ++k)
     rollout_sample(p, obst, J, x0, xref, st->U, st->S_e, beta, beta_d,
                    st->iter, k, Minv, &S[k], &coll[k], &minh[k],
-                   du + (size_t)k * T * 2);
+                   du + (size_t)k * T * 2, out && out->sens ? out->sens + k : NULL,
+                   out && out->reach ? out->reach + k : NULL);
 
   /* Eq. 4: weights and the weighted perturbation dU (held in Us), then
    * Algorithm 1's U* = U + SGF(dU), clamped to the box of Eq. 2. */
@@ -628,7 +678,7 @@ void orc_noise_batch(const orc_params* p, double S_e, int32_t K, int32_t T,
 int orc_sample_costs(const orc_params* p, const double* obst, int32_t J,
                      const double* x0, const double* xref, const orc_state* st,
                      const int32_t* ks, int32_t nk, double* S, uint8_t* coll,
-                     double* minh) {
+                     double* minh, double* sens, double* reach) {
   double beta_d, B0;
   orc_bsum(p, obst, J, p->x_goal, &beta_d, NULL, NULL);
   orc_bsum(p, obst, J, x0, &B0, NULL, NULL);
@@ -646,6 +696,7 @@ int orc_sample_costs(const orc_params* p, const double* obst, int32_t J,
 #endif
   for (int i = 0; i < nk; ++i)
     rollout_sample(p, obst, J, x0, xref, st->U, st->S_e, beta, beta_d, st->iter,
-                   ks[i], Minv, &S[i], &coll[i], &minh[i], NULL);
+                   ks[i], Minv, &S[i], &coll[i], &minh[i], NULL, sens ? sens + i : NULL,
+                   reach ? reach + i : NULL);
   return 0;
 }

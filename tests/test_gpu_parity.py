@@ -2,22 +2,25 @@
 element by element, on the same seeded inputs.
 
 Tolerances: per-sample cost-to-go within 1e-4 relative (relative to
-max(|S|, 1)), the updated control sequence U* within 1e-5 absolute, the set
+max(|S|, 1)), widened for samples that pass close to an obstacle by what
+the FP32 rollout's positions allow (cost_checks), the updated control
+sequence U* within 1e-5 absolute, the set
 of collided samples identical wherever the oracle's min h is farther than
 H_MARGIN from zero (closer samples are reported, not asserted).  Philox words
 are compared bit for bit."""
 import dataclasses
+import json
 import math
 
 import numpy as np
 import pytest
 
 from paper_2504_06437_gb300 import workloads as W
+from cost_checks import COST_RTOL, cost_errors
 from weight_checks import check_weights
 
 pytestmark = pytest.mark.gpu
 
-COST_RTOL = 1e-4
 U_ATOL = 1e-5
 H_MARGIN = 1e-4
 
@@ -34,9 +37,9 @@ def gpu():
 
 
 def compare_step(ro, dbg, u0, U_next, label="", lam=1.0):
-    S_o, S_g = ro["costs"], dbg["costs"]
-    rel = np.abs(S_g - S_o) / np.maximum(np.abs(S_o), 1.0)
-    assert rel.max() <= COST_RTOL, f"{label} cost rel err {rel.max():.3e} at k={rel.argmax()}"
+    rel_max, beyond, ratio, k = cost_errors(ro, dbg["costs"])
+    assert ratio <= 1.0, (f"{label} cost error {ratio:.3f} of its tolerance at k={k} "
+                          f"(largest relative error {rel_max:.3e}, {beyond} beyond {COST_RTOL})")
     sure = np.abs(ro["minh"]) > H_MARGIN
     mism = np.nonzero((ro["coll"] != dbg["coll"]) & sure)[0]
     assert mism.size == 0, f"{label} collided set differs at {mism[:10]}"
@@ -49,7 +52,7 @@ def compare_step(ro, dbg, u0, U_next, label="", lam=1.0):
     assert dbg["beta_d"] == pytest.approx(ro["beta_d"], rel=1e-5, abs=1e-6)
     assert dbg["CB_star"] == pytest.approx(ro["CB_star"], rel=1e-4, abs=1e-4)
     assert dbg["S_e_next"] == pytest.approx(ro["S_e_next"], rel=1e-5)
-    return dict(cost_rel=float(rel.max()),
+    return dict(cost_rel=rel_max, cost_beyond_rtol=beyond, cost_tol_ratio=ratio,
                 U_abs=float(np.abs(dbg["Ustar"] - ro["Ustar"]).max()),
                 w_abs=float(np.abs(dbg["weights"] - ro["weights"]).max()))
 
@@ -210,6 +213,23 @@ def test_quad_full_size_bench_config(gpu, orc):
     run_pair(gpu, orc, w, steps=1)
 
 
+def test_stress_three_steps_with_collisions(gpu, orc):
+    """The full stress workload (K 65536, T 100, 200 circles) for three
+    receding-horizon steps in the launch shape bench.py times, from a
+    nominal sequence that grazes the circle ahead of the start (thousands
+    of samples collide): every sample's cost, the collided set, U*, the
+    shifted sequence, C_B, S_e and the plant's barrier state carried into
+    the next step, against the oracle at each step.  Some samples pass
+    within h = 1e-3 of a circle without touching it; their costs are held
+    to the position-error term of the tolerance (cost_checks), which here
+    is what the FP32 rollout's positions allow."""
+    w = W.unicycle_stress(0)
+    T = int(w.params["T"])
+    u_init = np.tile(np.array([1.0, 0.5]), (T, 1))
+    errs = run_pair(gpu, orc, w, steps=3, tiling=bench_tiling(gpu, w), u_init=u_init)
+    print("STRESS3 " + json.dumps(errs))
+
+
 @pytest.mark.parametrize("shape", ["bench", "default"])
 def test_stress_config_sampled(gpu, orc, shape):
     """K=65536, T=100, 200 obstacles: many tile groups.  Costs of 512 sampled
@@ -230,8 +250,7 @@ def test_stress_config_sampled(gpu, orc, shape):
     ks = np.unique(np.concatenate([np.arange(0, p["K"], 131), [p["K"] - 1],
                                    np.argsort(dbg["costs"])[:32]]))
     ro = orc.sample_costs(p, w.obstacles, x, xref, ctl, ks)
-    rel = np.abs(dbg["costs"][ks] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
-    assert rel.max() <= COST_RTOL
+    assert cost_errors(ro, dbg["costs"][ks])[2] <= 1.0
     sure = np.abs(ro["minh"]) > H_MARGIN
     assert np.all((ro["coll"] == dbg["coll"][ks]) | ~sure)
     assert abs(dbg["weights"].sum() - 1.0) < 1e-6

@@ -14,8 +14,11 @@ float-pair sums with log-sum-exp merges.  Each case prints one line
 percentile relative cost error, the maximum absolute error of U* and of the
 weights, the relative error of the next exploration rate S_e, the number of
 collided samples, and the collided-set mismatches away from h = 0 (samples
-whose smallest |h| is within H_MARGIN are near-ties, counted separately); it
-asserts the tolerances (1e-4 relative cost, 1e-5 absolute U*, identical
+whose smallest |h| is within H_MARGIN are near-ties, counted separately),
+the number of samples beyond 1e-4 relative cost error and the largest ratio
+of a cost error to its tolerance; it asserts the tolerances (1e-4 relative
+cost, widened for samples that pass close to an obstacle by what the FP32
+rollout's positions allow: cost_checks; 1e-5 absolute U*; identical
 collided set away from near-ties)."""
 import json
 
@@ -23,11 +26,11 @@ import numpy as np
 import pytest
 
 from paper_2504_06437_gb300 import workloads as W
+from cost_checks import cost_errors
 from weight_checks import SELF_RTOL, weight_errors
 
 pytestmark = pytest.mark.gpu
 
-COST_RTOL = 1e-4
 U_ATOL = 1e-5
 H_MARGIN = 1e-4
 
@@ -117,6 +120,7 @@ def _compare(name, w, ro, ctl, u0, dbg, tiling, regs):
     """Checks one GPU step against the oracle's and prints its PRECISION line."""
     p = w.params
     rel = np.abs(dbg["costs"] - ro["costs"]) / np.maximum(np.abs(ro["costs"]), 1.0)
+    _, beyond, tol_ratio, _ = cost_errors(ro, dbg["costs"])
     u_err = float(np.abs(dbg["Ustar"] - ro["Ustar"]).max())
     w_err, w_self, w_ratio = weight_errors(ro, dbg, float(p["lambda"]))
     sure = np.abs(ro["minh"]) > H_MARGIN
@@ -125,6 +129,7 @@ def _compare(name, w, ro, ctl, u0, dbg, tiling, regs):
                tiling=[tiling["samples_per_cta"], tiling["threads"], tiling["positions_per_thread"]],
                kernel_regs=regs,
                cost_rel_max=float(rel.max()), cost_rel_p99=float(np.quantile(rel, 0.99)),
+               cost_beyond_rtol=beyond, cost_tolerance_ratio=tol_ratio,
                u_star_abs_max=u_err, u0_abs_max=float(np.abs(u0 - ro["u0"]).max()),
                weight_abs_max=w_err, weight_self_rel_max=w_self, weight_allowance_ratio=w_ratio,
                weight_sum_minus_1=float(dbg["weights"].sum() - 1.0),
@@ -132,7 +137,7 @@ def _compare(name, w, ro, ctl, u0, dbg, tiling, regs):
                collided=int(ro["coll"].sum()), collided_mismatch=mismatch,
                near_ties=int(np.sum(~sure)))
     print("PRECISION " + json.dumps(rec))
-    assert rel.max() <= COST_RTOL
+    assert tol_ratio <= 1.0
     assert u_err <= U_ATOL
     assert w_self <= SELF_RTOL
     assert w_ratio <= 1.0

@@ -791,3 +791,99 @@ def test_oracle_thread_count_does_not_change_results(orc):
     orc.set_threads(0)
     np.testing.assert_array_equal(outs[0]["costs"], outs[1]["costs"])
     np.testing.assert_array_equal(outs[0]["Ustar"], outs[1]["Ustar"])
+
+
+# ------------------------- barrier sensitivity behind the per-sample cost tolerance
+
+def _straight_cfg(**over):
+    """Every sample drives straight along +x at 1 m/s from the origin (the
+    control box is one point, so the draws do not matter), one shape point at
+    the body's origin, the goal far away (its barrier does not move)."""
+    base = dict(K=3, T=10, dt=0.05, u_min=[1.0, 0.0], u_max=[1.0, 0.0], h_eps=1e-6,
+                shape=np.zeros((1, 2)))
+    base.update(over)
+    p = _cfg(**base)
+    p["x_goal"] = np.array([1000.0, 1000.0, 0.0])
+    return p
+
+
+def _sens_by_differences(orc, p, shift_world, obst):
+    """-(dS/ds - dS/dbeta0 * dB(x0)/ds) for a translation s of the world along
+    x, every term by central differences of the oracle's own outputs; beta0 is
+    reached through the carried beta (first = False: beta0 = B(x0) -
+    gamma (beta_d - beta), so dS/dbeta0 = (dS/dbeta) / gamma)."""
+    x0 = np.zeros(3)
+    xref = np.zeros((p["T"] + 1, 3))
+
+    def cost(s=0.0, beta=0.0):
+        q, ob = shift_world(p, obst, s)
+        ctl = orc.new_controller(q)
+        ctl.first = False
+        ctl.beta = beta
+        return orc.step(q, ob, x0, xref, ctl)
+
+    d = 1e-5
+    dS = (cost(d)["costs"] - cost(-d)["costs"]) / (2 * d)
+    g = float(p["gamma_bas"])
+    if g > 0:
+        dS_dbeta0 = (cost(beta=d)["costs"] - cost(beta=-d)["costs"]) / (2 * d) / g
+        qa, oa = shift_world(p, obst, d)
+        qb, ob_ = shift_world(p, obst, -d)
+        dB0 = (orc.bsum(qa, oa, x0)[0] - orc.bsum(qb, ob_, x0)[0]) / (2 * d)
+        dS = dS - dS_dbeta0 * dB0
+    return -dS, cost()
+
+
+def _shift_circles(p, obst, s):
+    ob = np.array(obst, dtype=np.float64).copy()
+    ob[:, 0] += s
+    return p, ob
+
+
+@pytest.mark.parametrize("gamma, R_B", [(0.0, 1.0), (0.5, 2.0), (1.0, 0.3)])
+def test_barrier_sensitivity_is_the_cost_derivative_along_the_line(orc, gamma, R_B):
+    """Circles ahead on the line of motion: every barrier gradient along the
+    rollout points along x, so the sum of their norms (the oracle's sens)
+    equals the derivative of the cost-to-go with respect to moving the
+    circles along x, less the part that reaches the cost through the
+    barrier state at x0.  gamma 0, 0.5 and 1 cover the weights that Eq. 7's
+    recursion gives each step's barrier sum (1, a geometric sum, T - t);
+    reach is the 10 steps of 0.05 m."""
+    p = _straight_cfg(gamma_bas=gamma, R_B=R_B)
+    obst = np.array([[2.0, 0.0, 0.5], [3.5, 0.0, 0.3]])
+    want, r = _sens_by_differences(orc, p, _shift_circles, obst)
+    assert np.all(want > 0)
+    np.testing.assert_allclose(r["sens"], want, rtol=1e-6)
+    np.testing.assert_allclose(r["reach"], 0.5, rtol=1e-12)
+
+
+def test_barrier_sensitivity_grid_term_on_a_unit_ramp(orc):
+    """A grid map whose field is h = 3 - x (a signed distance with unit
+    gradient): moving the map along x moves every h by the same amount, so
+    the grid term's sensitivity 1 / h^2 per step is the cost's derivative
+    with respect to the map's origin (less the barrier state at x0)."""
+    p = _grid_cfg(lambda X, Y: 3.0 - X, K=3, T=10, dt=0.05, u_min=[1.0, 0.0],
+                  u_max=[1.0, 0.0], h_eps=1e-6, shape=np.zeros((1, 2)), gamma_bas=0.5)
+    p["x_goal"] = np.array([1000.0, 1000.0, 0.0])
+
+    def shift_map(q, obst, s):
+        q = dict(q)
+        q["grid_ox"] = p["grid_ox"] + s
+        return q, obst
+
+    want, r = _sens_by_differences(orc, p, shift_map, np.zeros((0, 3)))
+    assert np.all(want > 0)
+    np.testing.assert_allclose(r["sens"], want, rtol=1e-6)
+
+
+def test_barrier_sensitivity_zero_without_obstacles_and_floored_terms(orc):
+    """No obstacle, no term; a circle whose h stays below h_eps along the
+    whole rollout (the floored B does not move) adds nothing either."""
+    p = _straight_cfg(gamma_bas=0.5)
+    ctl = orc.new_controller(p)
+    r = orc.step(p, np.zeros((0, 3)), np.zeros(3), np.zeros((p["T"] + 1, 3)), ctl)
+    np.testing.assert_array_equal(r["sens"], 0.0)
+    p = _straight_cfg(gamma_bas=0.5, h_eps=10.0)
+    ctl = orc.new_controller(p)
+    r = orc.step(p, [[2.0, 0.0, 0.5]], np.zeros(3), np.zeros((p["T"] + 1, 3)), ctl)
+    np.testing.assert_array_equal(r["sens"], 0.0)
