@@ -213,21 +213,24 @@ def test_quad_full_size_bench_config(gpu, orc):
     run_pair(gpu, orc, w, steps=1)
 
 
-def test_stress_three_steps_with_collisions(gpu, orc):
-    """The full stress workload (K 65536, T 100, 200 circles) for three
-    receding-horizon steps in the launch shape bench.py times, from a
-    nominal sequence that grazes the circle ahead of the start (thousands
-    of samples collide): every sample's cost, the collided set, U*, the
-    shifted sequence, C_B, S_e and the plant's barrier state carried into
-    the next step, against the oracle at each step.  Some samples pass
-    within h = 1e-3 of a circle without touching it; their costs are held
-    to the position-error term of the tolerance (cost_checks), which here
-    is what the FP32 rollout's positions allow."""
-    w = W.unicycle_stress(0)
-    T = int(w.params["T"])
-    u_init = np.tile(np.array([1.0, 0.5]), (T, 1))
+@pytest.mark.parametrize("world", ["unicycle_stress", "quad2d_corridor"])
+def test_full_size_three_steps_with_collisions(gpu, orc, world):
+    """Full-size colliding worlds for three receding-horizon steps in the
+    launch shape bench.py times: the stress workload (K 65536, T 100, 200
+    circles) from a nominal sequence that grazes the circle ahead of the
+    start, and the quadrotor (K 4096, T 50, 7 shape points) with six circles
+    on its flight line; thousands of samples collide.  Every sample's cost,
+    the collided set, U*, the shifted sequence, C_B, S_e and the plant's
+    barrier state carried into the next step, against the oracle at each
+    step.  Some samples pass within h = 1e-3 of a circle without touching
+    it; their costs are held to the position-error term of the tolerance
+    (cost_checks), which there is what the FP32 rollout's positions allow."""
+    w = W.PRESETS[world](0)
+    u_init = None
+    if world == "unicycle_stress":
+        u_init = np.tile(np.array([1.0, 0.5]), (int(w.params["T"]), 1))
     errs = run_pair(gpu, orc, w, steps=3, tiling=bench_tiling(gpu, w), u_init=u_init)
-    print("STRESS3 " + json.dumps(errs))
+    print("THREE_STEPS " + world + " " + json.dumps(errs))
 
 
 @pytest.mark.parametrize("shape", ["bench", "default"])
