@@ -178,10 +178,10 @@ def oracle_rate(world, n_samples, min_seconds, max_steps=None, threads=None):
     ctl = oracle.new_controller(p)
     x = world.x_start
     xref = world.reference(x)
-    oracle.step(p, world.obstacles, x, xref, ctl)  # warm
+    oracle.step(p, world.obstacles, x, xref, ctl, want_sens=False)  # warm
     steps, t0 = 0, time.perf_counter()
     while True:
-        oracle.step(p, world.obstacles, x, xref, ctl)
+        oracle.step(p, world.obstacles, x, xref, ctl, want_sens=False)
         steps += 1
         el = time.perf_counter() - t0
         if (max_steps and steps >= max_steps) or (not max_steps and el >= min_seconds and steps >= 3):
@@ -269,7 +269,7 @@ def run_reference_mix(args):
         jobs.append((w, pp, oracle.new_controller(pp), w.reference(w.x_start)))
     def one():
         for w, pp, ctl, xr in jobs:
-            oracle.step(pp, w.obstacles, w.x_start, xr, ctl)
+            oracle.step(pp, w.obstacles, w.x_start, xr, ctl, want_sens=False)
     for _ in range(max(args.warmup, 3)):
         one()
     times = []
@@ -316,11 +316,11 @@ def run_reference(args, ws, rank):
     # at least 10 untimed steps: the oracle's first steps run well below its
     # steady rate (thread start-up, first touch of its buffers)
     for _ in range(max(args.warmup, 10)):
-        oracle.step(pp, world.obstacles, x, xref, ctl)
+        oracle.step(pp, world.obstacles, x, xref, ctl, want_sens=False)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.step(pp, world.obstacles, x, xref, ctl)
+        oracle.step(pp, world.obstacles, x, xref, ctl, want_sens=False)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = n_samples * pp["T"] / (ms / 1e3)

@@ -309,7 +309,7 @@ def new_controller(cfg: dict, u_init=None) -> Controller:
 
 
 def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
-         want_du: bool = False) -> dict:
+         want_du: bool = False, want_sens: bool = True) -> dict:
     """One Algorithm 1 iteration; mutates ``ctl`` (shift, S_e, beta, iter).
 
     ``xref`` is (T+1) x n.  Returns costs, coll, minh, weights, Ustar, u0,
@@ -317,7 +317,8 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
     (K x T x 2) when ``want_du``, and per sample ``sens`` (the barrier
     cost's first-order change per unit of position error at every shape
     point) and ``reach`` (the rollout's largest distance from x0), with
-    which the tests bound the cost error an FP32 rollout may make."""
+    which the tests bound the cost error an FP32 rollout may make (both zero
+    without ``want_sens``: the timed CPU baseline leaves them out)."""
     lib = _load()
     p = make_params(cfg)
     K, T, n = p.K, p.T, state_dim(p.model)
@@ -339,7 +340,8 @@ def step(cfg: dict, obstacles, x0, xref, ctl: Controller,
                minh=_dp(res["minh"]), weights=_dp(res["weights"]),
                du_eff=_dp(du) if want_du else C.POINTER(C.c_double)(),
                Ustar=_dp(res["Ustar"]), u0=_dp(res["u0"]),
-               sens=_dp(res["sens"]), reach=_dp(res["reach"]))
+               sens=_dp(res["sens"]) if want_sens else C.POINTER(C.c_double)(),
+               reach=_dp(res["reach"]) if want_sens else C.POINTER(C.c_double)())
     rc = lib.orc_step(C.byref(p), _dp(ob), ob.shape[0], _dp(x0), _dp(xref),
                       C.byref(st), C.byref(out))
     if rc == -2:
