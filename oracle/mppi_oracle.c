@@ -396,8 +396,10 @@ static void rollout_sample(const orc_params* p, const double* obst, int32_t J,
       const double dS_dB = p->R_B * (fabs(1.0 - g) > 1e-12 ? (1.0 - pow(g, m)) / (1.0 - g) : m);
       sens += dS_dB * bsum_grad(p, obst, J, x);
     }
-    const double dist = hypot(x[0] - x0[0], x[1] - x0[1]);
-    if (dist > reach) reach = dist;
+    if (reach_out) {
+      const double dist = hypot(x[0] - x0[0], x[1] - x0[1]);
+      if (dist > reach) reach = dist;
+    }
   }
   double phi = 0.0;
   for (int d = 0; d < n; ++d) {
